@@ -1,0 +1,125 @@
+"""Pins of the oracle's VIE entries (Eqs. 1-5) against what the mathematics fixes."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import entries as EN
+from oracle import quadrature as Q
+from oracle.dense import far_field, rcs, solve_dense
+from oracle.entries import Elements, rhs_planewave, tet_potentials, tri_potentials, zblock
+from oracle.mesh import build_mesh, swg_eval, tet_geometry
+
+
+def _brute_tri(r, A, B, C, n=300):
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    m1, m2 = (i + j) < n, (i + j) < n - 1
+    u = np.concatenate([(i[m1] + 1 / 3) / n, (i[m2] + 2 / 3) / n])
+    v = np.concatenate([(j[m1] + 1 / 3) / n, (j[m2] + 2 / 3) / n])
+    P = A + np.outer(u, B - A) + np.outer(v, C - A)
+    w = 0.5 * np.linalg.norm(np.cross(B - A, C - A)) / n ** 2
+    R = np.linalg.norm(P - r, axis=1)
+    return (w / R).sum(), (w * R).sum()
+
+
+def test_triangle_potentials_vs_brute_force():
+    A, B, C = np.array([0.0, 0, 0]), np.array([1.0, 0.2, 0]), np.array([0.3, 0.9, 0.1])
+    for r in ([0.4, 0.3, 0.5], [2.0, 1.0, 0.3], [-0.5, 0.2, 0.0], [0.5, 0.5, -0.8]):
+        r = np.array(r)
+        a, b = tri_potentials(r, A, B, C)
+        ra, rb = _brute_tri(r, A, B, C)
+        assert abs(a - ra) < 1e-5 * abs(ra) and abs(b - rb) < 1e-5 * abs(rb)
+
+
+def test_tet_potentials_vs_high_order_rule():
+    body = W.tiny_block(1, 1, 1, h=0.1)
+    geo = tet_geometry(build_mesh(body))
+    P, nrm = geo["P"][2], geo["normal"][2]
+    lam, w = Q.tet_conical(24)
+    pts = lam @ P
+    for r in ([0.3, 0.1, 0.2], [0.15, -0.05, 0.05]):
+        r = np.array(r)
+        U, Wv = tet_potentials(r[None, None], P[None], nrm[None])
+        R = np.linalg.norm(pts - r, axis=1)
+        ww = w * geo["vol"][2] / R
+        assert abs(U[0, 0] - ww.sum()) < 1e-10 * ww.sum()
+        assert np.allclose(Wv[0, 0], (ww[:, None] * (pts - r)).sum(0), rtol=1e-9, atol=1e-14)
+
+
+def test_zero_contrast_reduces_to_gram_and_projects_constants():
+    """kappa = 0 (eps_r = 1): Z is the SWG Gram matrix and a constant E_inc is reproduced exactly."""
+    body = W.tiny_block(2, 2, 1, h=0.1, eps=1.0)
+    mesh = build_mesh(body)
+    E = Elements(mesh, W.K0)
+    n = len(mesh["faces"])
+    Z = zblock(E, np.arange(n), np.arange(n))
+    assert np.allclose(Z.imag, 0.0, atol=1e-15)
+    assert np.allclose(Z, Z.T, atol=1e-15)
+    c = np.array([0.2, -0.7, 1.1])
+    # a constant field is a plane wave with k0 -> 0; use tiny k0 so the projection is exact
+    E0 = Elements(mesh, 1e-12)
+    V = rhs_planewave(E0, np.array([[0, 0, 1.0]]), c[None, :])
+    I = solve_dense(Z, V)[:, 0]
+    geo = E.geo
+    expect = np.array([c @ geo["normal"][mesh["face_tp"][f], mesh["face_lp"][f]] for f in range(n)])
+    assert np.allclose(I, expect, atol=1e-10)
+
+
+def test_symmetry_and_translation_invariance():
+    body = W.tiny_block(3, 2, 1, h=0.07, eps=3.0 - 0.2j)
+    mesh = build_mesh(body)
+    E = Elements(mesh, W.K0)
+    n = len(mesh["faces"])
+    Z = zblock(E, np.arange(n), np.arange(n))
+    # reciprocity of the Galerkin matrix for homogeneous kappa: Z = Z^T up to the quadrature
+    assert np.abs(Z - Z.T).max() < 2e-3 * np.abs(Z).max()
+    # the same body shifted by whole voxels gives the same matrix (to rounding)
+    sh = W.VoxelBody("shifted", body.h, body.ijk + np.array([5, -3, 7], dtype=np.int32), body.eps)
+    ms = build_mesh(sh)
+    Zs = zblock(Elements(ms, W.K0), np.arange(n), np.arange(n))
+    assert np.abs(Zs - Z).max() < 1e-11 * np.abs(Z).max()
+
+
+def test_quadrature_specification_converged():
+    """Brute force on a tiny input: raising every rule's order moves no entry by more than 1%."""
+    body = W.tiny_block(5, 1, 1, h=0.05, eps=4.0 - 0.5j)
+    mesh = build_mesh(body)
+    E = Elements(mesh, W.K0)
+    n = len(mesh["faces"])
+    Z = zblock(E, np.arange(n), np.arange(n))
+    saved = dict(EN.RULES)
+    try:
+        EN.RULES.update({
+            "far_tet": lambda: Q.tet_conical(4), "far_tri": lambda: Q.tri_conical(5),
+            "mid_tet": lambda: Q.tet_conical(4), "mid_tri": lambda: Q.tri_conical(5),
+            "near_tet": lambda: Q.tet_conical(6), "near_tri": lambda: Q.tri_conical(7),
+            "smooth_tet": lambda: Q.tet_conical(4), "smooth_tri": lambda: Q.tri_conical(5),
+        })
+        Zh = zblock(E, np.arange(n), np.arange(n))
+    finally:
+        EN.RULES.clear()
+        EN.RULES.update(saved)
+    err = np.abs(Z - Zh) / np.abs(Zh).max()
+    assert err.max() < 1e-2
+
+
+def test_energy_balance_lossy_sphere(lossy_sphere):
+    """Optical theorem: sigma_ext (forward amplitude) = sigma_sca + sigma_abs."""
+    E, Z, mesh = lossy_sphere["E"], lossy_sphere["Z"], lossy_sphere["mesh"]
+    k, p = W.planewave_x_along_z()
+    I = solve_dense(Z, rhs_planewave(E, k, p))
+    assert np.linalg.norm(Z @ I - rhs_planewave(E, k, p)) < 1e-12 * np.linalg.norm(rhs_planewave(E, k, p))
+    nt, npp = 40, 80
+    th = (np.arange(nt) + 0.5) * np.pi / nt
+    ph = np.arange(npp) * 2 * np.pi / npp
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    dirs = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+    s = rcs(E, I, dirs)[:, 0].reshape(nt, npp)
+    sig_sca = (s / (4 * np.pi) * np.sin(T)).sum() * (np.pi / nt) * (2 * np.pi / npp)
+    F = far_field(E, I, np.array([[0, 0, 1.0]]))[0, 0]
+    sig_ext = -4 * np.pi / W.K0 * np.imag(W.K0 ** 2 / (4 * np.pi) * F[0])  # exp(+j w t) convention
+    t = np.arange(len(mesh["tets"]))
+    r, w = E.tet_rule(t, Q.tet_conical(3))
+    d = np.einsum("tqad,ta->tqd", swg_eval(E.geo, t, r), I[:, 0][mesh["tet_faces"]])
+    e = d / mesh["eps"][:, None, None]
+    sig_abs = W.K0 * (np.abs(mesh["eps"].imag)[:, None] * w * (np.abs(e) ** 2).sum(-1)).sum()
+    assert abs(sig_ext - (sig_sca + sig_abs)) < 2e-3 * sig_ext
