@@ -1,0 +1,282 @@
+"""Benchmark: HOD-BF apply of the VIE system matrix on one GB300 (or N replicas).
+
+Workload: homogeneous lossy sphere, radius 2 lambda0, eps_r = 4 - 0.1j, voxel
+pitch lambda0/10 with 6 Kuhn tetrahedra per voxel (N = 410,208 SWG unknowns),
+HOD-BF with leaf 64 and chi_con = 1e-4, factors stored in complex FP32, one
+right-hand side.  A step is one application of the compressed operator
+Y = Z X (cluster-tree gather, every stage of the butterfly program, scatter).
+
+Metric: algorithmic bytes moved per apply / time, in GB/s, where the
+algorithmic bytes are 8 E + 16 N nrhs (E = complex entries of all stored
+factor blocks, c64; X read once, Y written once).  The factor data (tens of
+GB) is far larger than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--small]
+Under torchrun each rank builds its own replica (weak scaling, no collective on
+the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "HOD-BF apply GB/s (algorithmic bytes / apply time), single RHS"
+UNIT = "GB/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(small: bool):
+    if small:
+        return W.sphere(0.6, 4.0 - 0.1j, 1.0 / 10, name="sphere_r0.6_eps4-0.1j"), "sphere r=0.6 (small check)"
+    return W.sphere_large_c32(), "sphere r=2 lambda0, eps_r=4-0.1j, pitch lambda0/10, N=410208"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_apply_sample(seconds_budget: float = 20.0):
+    """Time the FP64 oracle's HOD-BF apply on a bounded sample of the workload (host cores)."""
+    from oracle.entries import Elements, zblock
+    from oracle.hodbf import HODBF, cluster_tree, face_centroids
+    from oracle.mesh import build_mesh
+
+    body = W.sphere(0.25, 4.0 - 0.1j, 1.0 / 16, name="sample")
+    mesh = build_mesh(body)
+    n = len(mesh["faces"])
+    Z = zblock(Elements(mesh, W.K0), np.arange(n), np.arange(n))
+    perm, LH, bounds = cluster_tree(face_centroids(mesh), 64)
+    Zt = Z[np.ix_(perm, perm)]
+    H = HODBF(lambda r, c: Zt[np.ix_(r, c)], bounds, LH, 1e-4)
+    x = W.random_block(n, 1, seed=1)
+    nbytes = 16 * H.entries() + 32 * n  # complex128 factors, x read and y written
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds_budget or reps < 3:
+        H.apply(x)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=nbytes / dt / 1e9, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"oracle FP64 HOD-BF apply of a sphere r=0.25 eps_r=4-0.1j pitch 1/16 (N={n}, "
+                       f"chi_con=1e-4, {H.entries()} entries), {reps} applies, {dt * 1e3:.1f} ms each",
+                ms_per_apply=dt * 1e3, n=n)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    base = oracle_apply_sample(5.0)
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(args.steps):
+        s = oracle_apply_sample(2.0)
+        vals.append(s["value"])
+    v = statistics.median(vals) if vals else base["value"]
+    _, desc = workload(args.small)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_apply"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": desc + " (oracle on a bounded sample)"},
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    line["cpu_baseline"]["value"] = v
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--small", action="store_true", help="small workload (quick functional check)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2111_01730_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    hbm, peak_kind = peaks()
+    body, desc = workload(args.small)
+    t0 = time.perf_counter()
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c64", seed=1)
+    build_s = time.perf_counter() - t0
+    st = op.get_stats()
+    n = op.n
+    entries, sbytes, tiles = op.program_info(pkg.VIE_OP_Z)
+    E = int(entries.sum())
+    alg_bytes = 8 * E + 16 * n  # per apply, nrhs = 1
+    x = torch.from_numpy(W.random_block(n, 1, seed=7)[:, 0].astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        op.apply(x, y)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        op.apply(x, y)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    # per-stage timing of the dominant kernel (stage kernels), CUDA events on the launch stream
+    prof = []
+    for _ in range(5):
+        ms, launches = op.apply_profile(x, y)
+        prof.append(ms)
+    clk = clocks.stop()
+    prof = np.median(np.array(prof), axis=0)
+    stage_ms = prof[1:-1]
+    launches_per_apply = int(launches)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * alg_bytes / (ms_step * 1e-3) / 1e9
+    # end to end through the public API: pinned host X -> device, apply, device -> host Y
+    xh = torch.from_numpy(W.random_block(n, 1, seed=8)[:, 0].astype(np.complex64)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(3):
+        xd.copy_(xh, non_blocking=True)
+        op.apply(xd, y)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        op.apply(xd, y)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    # roofline of the dominant kernel: the stage kernel, all its launches of one apply
+    stage_alg = 8 * E
+    achieved = stage_alg / (stage_ms.sum() * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "levels": st.levels, "chi_con": 1e-4, "leaf": 64, "nrhs": 1,
+                       "factor_entries": E, "factor_bytes_stored": int(sbytes.sum()), "max_rank": st.max_rank,
+                       "build_seconds": round(build_s, 2), "l2": "inputs (factor data) larger than L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "apply_latency_ms": {"p50": round(float(np.percentile(per, 50)), 4),
+                                 "p99": round(float(np.percentile(per, 99)), 4)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": None,
+                         "kernel": "stage_kernel<float,float,1> (all stages of one apply)",
+                         "peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms]},
+            "e2e": {"value": round(alg_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": launches_per_apply * args.steps,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            cb = oracle_apply_sample(15.0)
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

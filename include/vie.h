@@ -1,0 +1,182 @@
+/*
+ * vie.h — C ABI of the GB300 butterfly-accelerated VIE library.
+ *
+ * The library applies the HOD-BF compressed Galerkin system matrix Z of the
+ * D-VIE and its HOD-BF approximate inverse Zinv to blocks of vectors, and
+ * builds both on one GPU (sm_103a).
+ *
+ *   Problem (Sec. II, Eqs. 1-5): D/eps - j w eta0 L[kappa D] = E_inc in V,
+ *   discretized with one SWG function per face of a tetrahedral mesh and
+ *   Galerkin testing, Z I = V.  Preconditioned solve (Eq. 6).
+ *   HOD-BF (Sec. III-A, Eqs. 7-10): dense leaf blocks D_tau plus butterfly
+ *   factorizations of every sibling off-diagonal block B_tau.
+ *   Inverse (Sec. III-B, Algorithms 1-2).
+ *
+ * Units: lambda0 = 1 (k0 = 2 pi for the paper's normalization is passed
+ * explicitly), time convention exp(+j w t), so lossy media have Im eps_r < 0.
+ * Complex numbers are interleaved (re, im) pairs: c64 = 2 x float,
+ * c128 = 2 x double.  Vectors are column-major N x nrhs blocks in the
+ * ORIGINAL face order of the mesh (faces numbered as described at
+ * vie_mesh_faces).
+ *
+ * Ownership: the caller owns every array it passes; the library owns the
+ * operator (vie_op) and its device memory until vie_destroy.  Device pointers
+ * must be on the current CUDA device.  All calls taking a `stream` are
+ * stream-ordered (cudaStream_t passed as void*, NULL = legacy default stream)
+ * and return without synchronizing unless they write a host out-parameter.
+ *
+ * Errors: every call returns a vie_status; VIE_OK = 0.  No call aborts the
+ * process.  vie_last_error() returns a thread-local message for the last
+ * failing call on the calling thread.
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vie_op vie_op; /* opaque */
+
+typedef enum {
+  VIE_OK = 0,
+  VIE_EINVAL = -1,    /* invalid argument (null pointer, bad size, bad enum)     */
+  VIE_ENOMEM = -2,    /* device or host allocation failed                       */
+  VIE_ENOTCONV = -3,  /* iterative solve stopped before reaching the tolerance  */
+  VIE_ETIMEOUT = -4,  /* a bounded device wait ran out                          */
+  VIE_ENAN = -5,      /* NaN or Inf found in an input or a result               */
+  VIE_ECUDA = -6,     /* a CUDA runtime call failed                             */
+  VIE_ENOTSUP = -7    /* the operator lacks what the call needs (e.g. no Zinv)  */
+} vie_status;
+
+typedef enum { VIE_OP_Z = 0, VIE_OP_ZINV = 1 } vie_opkind;
+typedef enum { VIE_C64 = 0, VIE_C128 = 1 } vie_dtype;
+
+/* A scatterer on a cubic voxel lattice of pitch h: voxel (i, j, k) is the cube
+ * [i h, (i+1) h] x [j h, (j+1) h] x [k h, (k+1) h].  Each voxel is split into
+ * the 6 Kuhn tetrahedra (Sec. II mesh, reading of the voxel mesh rule).
+ * ijk: host, 3*nvox int32, no duplicates; eps: host, 2*nvox doubles
+ * (re, im) relative permittivity per voxel. */
+typedef struct {
+  int64_t nvox;
+  const int32_t* ijk;
+  const double* eps;
+  double h;
+} vie_voxels;
+
+typedef struct {
+  double tol_con;      /* chi_con: ID truncation |R_kk| <= tol |R_11| (Eq. 7) */
+  double tol_fact;     /* chi_fact of the inverse (Sec. III-B); <= 0: no Zinv  */
+  int32_t leaf;        /* max unknowns per leaf of the cluster tree (64)        */
+  int32_t factor_dtype;/* vie_dtype of the stored factors (VIE_C64 default)     */
+  uint64_t seed;       /* seed of the row sampling in the IDs                   */
+  int32_t oversample;  /* extra random rows per ID beyond the candidate count   */
+  int32_t reserved;
+} vie_config;
+
+typedef struct {
+  int64_t n;              /* unknowns = faces of the mesh                       */
+  int64_t ntets;
+  int32_t levels;         /* L_H                                                */
+  int32_t max_rank;       /* max butterfly rank over all blocks                 */
+  int64_t entries_z;      /* complex entries stored for Z (leaf + butterflies)  */
+  int64_t entries_zinv;   /* complex entries stored for Zinv (0 if none)        */
+  int64_t bytes_z;        /* bytes of the stored Z factors (incl. padding)      */
+  int64_t bytes_zinv;
+  int64_t entries_evaluated; /* matrix entries evaluated during the build       */
+  double build_seconds;
+  double invert_seconds;
+  int32_t apply_stages_z; /* kernel stages of one Z apply                       */
+  int32_t apply_stages_zinv;
+} vie_stats_t;
+
+/* Build Z (and Zinv when cfg->tol_fact > 0) for the voxel body at wavenumber
+ * k0 (Sec. III-A construction; Sec. III-B inversion).  Mesh, SWG table and
+ * cluster tree are made on the host; entries, IDs and factors on the GPU.
+ * Returns VIE_EINVAL for nvox <= 0, h <= 0, leaf < 4, tol_con <= 0. */
+vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg,
+                     void* stream, vie_op** out);
+
+/* Y = op(X) for op = Z or Zinv, X and Y device arrays, N x nrhs column-major
+ * with leading dimensions ldx, ldy >= N (in elements), dtype VIE_C64 or
+ * VIE_C128 for both.  The factors keep their stored type; accumulation runs
+ * in the vector type (c128 vectors give the FP64-accumulated apply used for
+ * refinement residuals).  X and Y must not overlap.  (Sec. III-A: "storage
+ * and application costs ... O(n log n)"; Algorithm 1 for Zinv.) */
+vie_status vie_apply(vie_op* op, int32_t which, const void* X, void* Y, int64_t nrhs,
+                     int64_t ldx, int64_t ldy, int32_t dtype, void* stream);
+
+/* vie_apply that also times each kernel of the apply with CUDA events on
+ * `stream` and waits for it: ms (host, cap >= stages + 2) receives the
+ * milliseconds of [gather, stage 0 .. stage S-1, scatter]; *launches (may be
+ * NULL) the number of kernel launches of one apply.  Metrics/profiling aid;
+ * same arguments and errors as vie_apply, plus VIE_EINVAL if cap is short. */
+vie_status vie_apply_profile(vie_op* op, int32_t which, const void* X, void* Y, int64_t nrhs,
+                             int64_t ldx, int64_t ldy, int32_t dtype, void* stream, double* ms,
+                             int64_t* launches, int32_t cap);
+
+/* Per-stage layout of an operator's apply program: *nstages receives the
+ * stage count S; entries[i] (complex entries of the factor blocks of stage i,
+ * the algorithmic count), bytes[i] (stored bytes incl. row padding) and
+ * tiles[i] (warp tiles) are written for i < min(S, cap).  Host arrays; any
+ * of them may be NULL. */
+vie_status vie_program_info(const vie_op* op, int32_t which, int64_t* entries, int64_t* bytes,
+                            int64_t* tiles, int32_t cap, int32_t* nstages);
+
+/* out[i] = Z(rows[i], cols[i]) for i < count, evaluated on the GPU in FP64
+ * from Eq. (5) (entries of the uncompressed matrix).  rows, cols: device int32
+ * face indices in [0, N); out: device c128. */
+vie_status vie_entries(vie_op* op, const int32_t* rows, const int32_t* cols, int64_t count,
+                       void* out, void* stream);
+
+/* V(:, j) = <f_m, pol_j exp(-j k0 khat_j . r)> (Eq. 5) for j < nrhs.
+ * khat, pol: host, 3*nrhs doubles; V: device c128, N x nrhs (ld = N). */
+vie_status vie_rhs_planewave(vie_op* op, const double* khat, const double* pol, int64_t nrhs,
+                             void* V, void* stream);
+
+/* Solve Z I = V with right-preconditioned restarted GMRES (Zinv as the
+ * preconditioner when present, Eq. 6) inside FP64 iterative refinement.
+ * V, I: device c128 N x nrhs (ld = N).  iters, relres: host arrays of nrhs
+ * (may be NULL).  Returns VIE_ENOTCONV (I holds the best iterate) when a
+ * column misses rtol within max_iter inner iterations. */
+vie_status vie_solve(vie_op* op, const void* V, void* I, int64_t nrhs, double rtol,
+                     int32_t restart, int32_t max_iter, int32_t* iters, double* relres,
+                     void* stream);
+
+/* Bistatic RCS sigma(dir_k) for each column of I (device c128 N x nrhs) and
+ * each unit direction dirs (host 3*ndir): rcs (host, ndir x nrhs, column
+ * major), in lambda0^2, sigma = k0^4/(4 pi) |(I - rr) . F|^2,
+ * F = int kappa d exp(j k0 rhat . r) dv. */
+vie_status vie_farfield(vie_op* op, const void* I, int64_t nrhs, const double* dirs, int64_t ndir,
+                        double* rcs, void* stream);
+
+/* Face table of the mesh: faces (host 3*N int32, sorted vertex ids, faces
+ * sorted lexicographically), tp / tm (host N int32: the lower / higher tet
+ * id holding the face, tm = -1 on the boundary).  Vertices are the lattice
+ * points sorted lexicographically by (i, j, k); tets are voxel-major, then
+ * the 6 axis permutations in lexicographic order.  Any pointer may be NULL. */
+vie_status vie_mesh_faces(const vie_op* op, int32_t* faces, int32_t* tp, int32_t* tm);
+
+/* Host only (no GPU needed): the mesh and cluster tree that vie_build would
+ * make for `body`.  *n receives N; when non-NULL, faces (3*N), tp, tm (N) are
+ * filled as in vie_mesh_faces, perm (N) as in vie_tree_perm and *levels with
+ * L_H.  Call once with NULL arrays to size them. */
+vie_status vie_mesh_host(const vie_voxels* body, int32_t leaf, int64_t* n, int32_t* faces, int32_t* tp,
+                         int32_t* tm, int32_t* perm, int32_t* levels);
+
+/* perm (host, N int32): original face index at each position of the cluster
+ * tree order (Sec. III-A: KD bisection to a complete tree of L_H levels). */
+vie_status vie_tree_perm(const vie_op* op, int32_t* perm);
+
+vie_status vie_stats(const vie_op* op, vie_stats_t* out);
+
+void vie_destroy(vie_op* op);
+const char* vie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIE_H */

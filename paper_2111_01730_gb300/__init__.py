@@ -1,0 +1,270 @@
+"""GB300 butterfly-accelerated VIE: Python binding of the C ABI in include/vie.h.
+
+Argument marshalling only: every step of the build, the apply and the solve
+runs in libvie.so (CUDA, sm_103a).  PyTorch provides device memory and streams.
+There is no CPU fallback: loading fails loudly when the library is missing.
+
+Vectors are complex CUDA tensors of shape (N,) or (N, nrhs) in column-major
+layout (``t.stride(0) == 1``), indexed by the faces of the mesh in the
+library's face order (see ``Operator.faces``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvie.so")
+
+VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ENOTCONV, VIE_ETIMEOUT, VIE_ENAN, VIE_ECUDA, VIE_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+VIE_OP_Z, VIE_OP_ZINV = 0, 1
+VIE_C64, VIE_C128 = 0, 1
+
+# every symbol declared in include/vie.h
+EXPORTS = ["vie_build", "vie_apply", "vie_apply_profile", "vie_program_info", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
+           "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_destroy", "vie_last_error"]
+
+
+class VieError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"vie status {status}: {msg}")
+        self.status = status
+
+
+class _Voxels(ctypes.Structure):
+    _fields_ = [("nvox", ctypes.c_int64), ("ijk", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("h", ctypes.c_double)]
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("tol_con", ctypes.c_double), ("tol_fact", ctypes.c_double), ("leaf", ctypes.c_int32),
+                ("factor_dtype", ctypes.c_int32), ("seed", ctypes.c_uint64), ("oversample", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ntets", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("max_rank", ctypes.c_int32), ("entries_z", ctypes.c_int64), ("entries_zinv", ctypes.c_int64),
+                ("bytes_z", ctypes.c_int64), ("bytes_zinv", ctypes.c_int64), ("entries_evaluated", ctypes.c_int64),
+                ("build_seconds", ctypes.c_double), ("invert_seconds", ctypes.c_double),
+                ("apply_stages_z", ctypes.c_int32), ("apply_stages_zinv", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libvie.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libvie.so not found at {path}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "vie_build": [P, D, P, P, P],
+        "vie_apply": [P, I32, P, P, I64, I64, I64, I32, P],
+        "vie_entries": [P, P, P, I64, P, P],
+        "vie_apply_profile": [P, I32, P, P, I64, I64, I64, I32, P, P, P, I32],
+        "vie_program_info": [P, I32, P, P, P, I32, P],
+        "vie_rhs_planewave": [P, P, P, I64, P, P],
+        "vie_solve": [P, P, P, I64, D, I32, I32, P, P, P],
+        "vie_farfield": [P, P, I64, P, I64, P, P],
+        "vie_mesh_faces": [P, P, P, P],
+        "vie_mesh_host": [P, I32, P, P, P, P, P, P],
+        "vie_tree_perm": [P, P],
+        "vie_stats": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.vie_destroy.argtypes = [P]
+    lib.vie_destroy.restype = None
+    lib.vie_last_error.argtypes = []
+    lib.vie_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != VIE_OK:
+        raise VieError(status, _lib.vie_last_error().decode())
+
+
+def _stream_ptr(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _colmajor(t, n):
+    """(N,) or (N, nrhs) complex tensor -> (tensor, nrhs, ld) with stride(0) == 1."""
+    if t.dim() == 1:
+        t = t.reshape(n, 1)
+    nrhs = t.shape[1]
+    if t.stride(0) != 1 or (nrhs > 1 and t.stride(1) < n):
+        t = t.t().contiguous().t()
+    return t, nrhs, (t.stride(1) if nrhs > 1 else n)
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.complex64:
+        return VIE_C64
+    if t.dtype == torch.complex128:
+        return VIE_C128
+    raise TypeError(f"complex64 or complex128 tensor expected, got {t.dtype}")
+
+
+def _voxels(body):
+    ijk = np.ascontiguousarray(body.ijk, dtype=np.int32)
+    eps = np.ascontiguousarray(np.stack([np.real(body.eps), np.imag(body.eps)], 1), dtype=np.float64)
+    return _Voxels(len(ijk), ijk.ctypes.data, eps.ctypes.data, float(body.h)), (ijk, eps)
+
+
+def mesh_host(body, leaf: int = 64):
+    """Mesh face table and cluster-tree permutation made by the library on the host (no GPU)."""
+    lib = load_library()
+    vox, keep = _voxels(body)
+    n = ctypes.c_int64(0)
+    _check(lib.vie_mesh_host(ctypes.byref(vox), leaf, ctypes.byref(n), None, None, None, None, None))
+    N = n.value
+    f = np.zeros((N, 3), dtype=np.int32)
+    tp = np.zeros(N, dtype=np.int32)
+    tm = np.zeros(N, dtype=np.int32)
+    perm = np.zeros(N, dtype=np.int32)
+    lev = ctypes.c_int32(0)
+    _check(lib.vie_mesh_host(ctypes.byref(vox), leaf, ctypes.byref(n), f.ctypes.data, tp.ctypes.data,
+                             tm.ctypes.data, perm.ctypes.data, ctypes.byref(lev)))
+    return dict(faces=f, tp=tp, tm=tm, perm=perm, levels=lev.value)
+
+
+class Operator:
+    """A HOD-BF compressed VIE operator Z (and Zinv) resident on the current GPU."""
+
+    def __init__(self, body, k0: float, tol_con: float = 1e-4, tol_fact: float = 0.0, leaf: int = 64,
+                 factor_dtype: str = "c64", seed: int = 1, oversample: int = 10, stream=None):
+        lib = load_library()
+        self._h = ctypes.c_void_p()
+        ijk = np.ascontiguousarray(body.ijk, dtype=np.int32)
+        eps = np.ascontiguousarray(np.stack([np.real(body.eps), np.imag(body.eps)], 1), dtype=np.float64)
+        vox = _Voxels(len(ijk), ijk.ctypes.data, eps.ctypes.data, float(body.h))
+        cfg = _Config(tol_con, tol_fact, leaf, VIE_C64 if factor_dtype == "c64" else VIE_C128, seed, oversample, 0)
+        _check(lib.vie_build(ctypes.byref(vox), float(k0), ctypes.byref(cfg), _stream_ptr(stream),
+                             ctypes.byref(self._h)))
+        self.stats = self.get_stats()
+        self.n = int(self.stats.n)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and h.value and _lib is not None:
+            _lib.vie_destroy(h)
+            self._h = ctypes.c_void_p()
+
+    def close(self):
+        self.__del__()
+
+    def get_stats(self) -> Stats:
+        st = Stats()
+        _check(_lib.vie_stats(self._h, ctypes.byref(st)))
+        return st
+
+    def apply(self, X, Y=None, op: int = VIE_OP_Z, stream=None):
+        """Y = Z X (op = VIE_OP_Z) or Zinv X; X complex CUDA tensor (N,) or (N, nrhs)."""
+        import torch
+
+        squeeze = X.dim() == 1
+        Xc, nrhs, ldx = _colmajor(X, self.n)
+        if Y is None:
+            Y = torch.empty((nrhs, self.n), dtype=X.dtype, device=X.device).t()
+        Yc, _, ldy = _colmajor(Y, self.n)
+        assert Yc.data_ptr() == Y.data_ptr() or Y.dim() == 1, "Y must be column-major"
+        _check(_lib.vie_apply(self._h, op, ctypes.c_void_p(Xc.data_ptr()), ctypes.c_void_p(Yc.data_ptr()), nrhs,
+                              ldx, ldy, _dtype_code(Xc), _stream_ptr(stream)))
+        return Yc[:, 0] if squeeze else Yc
+
+    def apply_profile(self, X, Y, op: int = VIE_OP_Z, stream=None):
+        """Apply with per-kernel CUDA-event times: (ms array [gather, stages..., scatter], launches)."""
+        Xc, nrhs, ldx = _colmajor(X, self.n)
+        Yc, _, ldy = _colmajor(Y, self.n)
+        ms = np.zeros(64, dtype=np.float64)
+        launches = ctypes.c_int64(0)
+        _check(_lib.vie_apply_profile(self._h, op, ctypes.c_void_p(Xc.data_ptr()), ctypes.c_void_p(Yc.data_ptr()),
+                                      nrhs, ldx, ldy, _dtype_code(Xc), _stream_ptr(stream), ms.ctypes.data,
+                                      ctypes.byref(launches), 64))
+        ns = self.program_info(op)[0].size + 2
+        return ms[:ns], launches.value
+
+    def program_info(self, op: int = VIE_OP_Z):
+        """Per-stage (entries, bytes, tiles) numpy arrays of the apply program."""
+        e = np.zeros(64, dtype=np.int64)
+        b = np.zeros(64, dtype=np.int64)
+        t = np.zeros(64, dtype=np.int64)
+        ns = ctypes.c_int32(0)
+        _check(_lib.vie_program_info(self._h, op, e.ctypes.data, b.ctypes.data, t.ctypes.data, 64, ctypes.byref(ns)))
+        return e[:ns.value], b[:ns.value], t[:ns.value]
+
+    def entries(self, rows, cols, stream=None):
+        """Z(rows[i], cols[i]) in FP64 (int32 CUDA tensors) -> complex128 CUDA tensor."""
+        import torch
+
+        rows = rows.to(torch.int32).contiguous()
+        cols = cols.to(torch.int32).contiguous()
+        out = torch.empty(rows.numel(), dtype=torch.complex128, device=rows.device)
+        _check(_lib.vie_entries(self._h, ctypes.c_void_p(rows.data_ptr()), ctypes.c_void_p(cols.data_ptr()),
+                                rows.numel(), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def rhs_planewave(self, khat, pol, stream=None):
+        import torch
+
+        khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+        pol = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.float64)
+        nrhs = len(khat)
+        V = torch.empty((nrhs, self.n), dtype=torch.complex128, device="cuda").t()
+        _check(_lib.vie_rhs_planewave(self._h, khat.ctypes.data, pol.ctypes.data, nrhs,
+                                      ctypes.c_void_p(V.data_ptr()), _stream_ptr(stream)))
+        return V
+
+    def solve(self, V, rtol=1e-6, restart=30, max_iter=500, stream=None):
+        import torch
+
+        Vc, nrhs, ld = _colmajor(V.to(torch.complex128), self.n)
+        assert ld == self.n
+        I = torch.empty((nrhs, self.n), dtype=torch.complex128, device=V.device).t()
+        iters = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        st = _lib.vie_solve(self._h, ctypes.c_void_p(Vc.data_ptr()), ctypes.c_void_p(I.data_ptr()), nrhs,
+                            float(rtol), restart, max_iter, iters.ctypes.data, rel.ctypes.data, _stream_ptr(stream))
+        if st not in (VIE_OK, VIE_ENOTCONV):
+            _check(st)
+        return I, iters, rel, st
+
+    def farfield_rcs(self, I, dirs, stream=None):
+        Ic, nrhs, ld = _colmajor(I, self.n)
+        assert ld == self.n
+        dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        out = np.zeros((nrhs, len(dirs)), dtype=np.float64)
+        _check(_lib.vie_farfield(self._h, ctypes.c_void_p(Ic.data_ptr()), nrhs, dirs.ctypes.data, len(dirs),
+                                 out.ctypes.data, _stream_ptr(stream)))
+        return out.T
+
+    def faces(self):
+        f = np.zeros((self.n, 3), dtype=np.int32)
+        tp = np.zeros(self.n, dtype=np.int32)
+        tm = np.zeros(self.n, dtype=np.int32)
+        _check(_lib.vie_mesh_faces(self._h, f.ctypes.data, tp.ctypes.data, tm.ctypes.data))
+        return f, tp, tm
+
+    def tree_perm(self):
+        p = np.zeros(self.n, dtype=np.int32)
+        _check(_lib.vie_tree_perm(self._h, p.ctypes.data))
+        return p

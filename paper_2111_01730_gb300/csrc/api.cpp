@@ -1,0 +1,281 @@
+// C ABI of libvie (declared in include/vie.h).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace vie {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+void DevBuf::alloc(size_t n) {
+  release();
+  if (n == 0) n = 16;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    throw Error{VIE_ENOMEM, std::string("cudaMalloc(") + std::to_string(n) + "): " + cudaGetErrorString(e)};
+  }
+  bytes = n;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+void ensure_ws(vie_op* h, const Program& p, int64_t nrhs, int dtype) {
+  size_t es = dtype == VIE_C64 ? 8 : 16;
+  size_t need = es * (size_t)nrhs * (size_t)std::max<int64_t>(p.n, 1);
+  size_t needc = es * (size_t)nrhs * (size_t)std::max<int64_t>(p.ncoef, 1);
+  if (h->xt.bytes < need) { h->xt.alloc(need); h->yt.alloc(need); }
+  if (h->coef.bytes < needc) h->coef.alloc(needc);
+}
+
+void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dtype, cudaStream_t s) {
+  const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+  ensure_ws(h, p, nrhs, dtype);
+  program_apply(p, h->perm.as<int32_t>(), X, Y, nrhs, h->mesh.nf, h->mesh.nf, dtype, h->xt.p, h->yt.p, h->coef.p, s);
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+template <class F>
+static vie_status guarded(F&& f) {
+  try {
+    f();
+    return VIE_OK;
+  } catch (const Error& e) {
+    set_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return VIE_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error(e.what());
+    return VIE_EINVAL;
+  }
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+extern "C" {
+
+const char* vie_last_error(void) { return g_err.c_str(); }
+
+vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, void* stream, vie_op** out) {
+  return guarded([&] {
+    VIE_REQUIRE(body && cfg && out, VIE_EINVAL, "null argument");
+    VIE_REQUIRE(body->nvox > 0 && body->ijk && body->eps && body->h > 0, VIE_EINVAL, "empty or invalid voxel body");
+    VIE_REQUIRE(cfg->leaf >= 4 && cfg->tol_con > 0 && k0 > 0, VIE_EINVAL, "invalid configuration");
+    VIE_REQUIRE(cfg->factor_dtype == VIE_C64 || cfg->factor_dtype == VIE_C128, VIE_EINVAL, "factor dtype");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    double t0 = now_s();
+    vie_op* h = new vie_op();
+    try {
+      h->cfg = *cfg;
+      if (h->cfg.oversample <= 0) h->cfg.oversample = 10;
+      build_mesh(*body, h->mesh);
+      geometry_upload(h->mesh, k0, h->geo, s);
+      geometry_table(h->geo, s);
+      // face centroids and cluster tree
+      const int64_t N = h->mesh.nf;
+      std::vector<double> pts(3 * N);
+      for (int64_t f = 0; f < N; ++f)
+        for (int d = 0; d < 3; ++d) {
+          double a = double(h->mesh.vlat[3 * h->mesh.faces[3 * f] + d]) * h->mesh.h;
+          double b = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 1] + d]) * h->mesh.h;
+          double c = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 2] + d]) * h->mesh.h;
+          pts[3 * f + d] = ((a + b) + c) / 3.0;
+        }
+      build_tree(pts, cfg->leaf, h->tree);
+      h->perm.alloc(sizeof(int32_t) * N);
+      VIE_CUDA(cudaMemcpyAsync(h->perm.p, h->tree.perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+      h->tet_faces.alloc(sizeof(int32_t) * 4 * h->mesh.nt);
+      VIE_CUDA(cudaMemcpyAsync(h->tet_faces.p, h->mesh.tet_faces.data(), sizeof(int32_t) * 4 * h->mesh.nt,
+                               cudaMemcpyHostToDevice, s));
+      BuildResult br;
+      build_hodbf(h, s, br);
+      VIE_CUDA(cudaStreamSynchronize(s));
+      h->stats.n = N;
+      h->stats.ntets = h->mesh.nt;
+      h->stats.levels = h->tree.levels;
+      h->stats.max_rank = br.max_rank;
+      h->stats.entries_z = h->z.entries;
+      h->stats.bytes_z = h->z.bytes;
+      h->stats.entries_evaluated = br.entries_evaluated;
+      h->stats.apply_stages_z = (int32_t)h->z.stages.size();
+      h->stats.build_seconds = now_s() - t0;
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+void vie_destroy(vie_op* op) { delete op; }
+
+vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t nrhs, int64_t ldx, int64_t ldy,
+                     int32_t dtype, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h && X && Y, VIE_EINVAL, "null argument");
+    VIE_REQUIRE(nrhs >= 1 && ldx >= h->mesh.nf && ldy >= h->mesh.nf, VIE_EINVAL, "bad nrhs or leading dimension");
+    VIE_REQUIRE(dtype == VIE_C64 || dtype == VIE_C128, VIE_EINVAL, "bad dtype");
+    VIE_REQUIRE(which == VIE_OP_Z || which == VIE_OP_ZINV, VIE_EINVAL, "bad operator kind");
+    VIE_REQUIRE(which == VIE_OP_Z || h->has_zinv, VIE_ENOTSUP, "operator has no inverse (tol_fact <= 0)");
+    const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    ensure_ws(h, p, nrhs, dtype);
+    program_apply(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p,
+                  (cudaStream_t)stream);
+  });
+}
+
+vie_status vie_apply_profile(vie_op* h, int32_t which, const void* X, void* Y, int64_t nrhs, int64_t ldx,
+                             int64_t ldy, int32_t dtype, void* stream, double* ms, int64_t* launches, int32_t cap) {
+  return guarded([&] {
+    VIE_REQUIRE(h && X && Y && ms, VIE_EINVAL, "null argument");
+    VIE_REQUIRE(nrhs >= 1 && ldx >= h->mesh.nf && ldy >= h->mesh.nf, VIE_EINVAL, "bad nrhs or leading dimension");
+    VIE_REQUIRE(dtype == VIE_C64 || dtype == VIE_C128, VIE_EINVAL, "bad dtype");
+    VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
+    const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    const int ns = (int)p.stages.size() + 2;
+    VIE_REQUIRE(cap >= ns, VIE_EINVAL, "ms array too short (stages + 2 needed)");
+    ensure_ws(h, p, nrhs, dtype);
+    std::vector<cudaEvent_t> ev(ns + 1);
+    for (auto& e : ev) VIE_CUDA(cudaEventCreate(&e));
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+      program_apply(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p, s, ev.data());
+      VIE_CUDA(cudaEventSynchronize(ev[ns]));
+      for (int i = 0; i < ns; ++i) {
+        float t = 0;
+        VIE_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+        ms[i] = t;
+      }
+      if (launches) *launches = program_launches(p, nrhs);
+    } catch (...) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      throw;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+  });
+}
+
+vie_status vie_program_info(const vie_op* h, int32_t which, int64_t* entries, int64_t* bytes, int64_t* launches,
+                            int32_t cap, int32_t* nstages) {
+  return guarded([&] {
+    VIE_REQUIRE(h && nstages, VIE_EINVAL, "null argument");
+    VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
+    const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    *nstages = (int32_t)p.stages.size();
+    for (int i = 0; i < (int)p.stages.size() && i < cap; ++i) {
+      if (entries) entries[i] = p.stages[i].entries;
+      if (bytes) bytes[i] = p.stages[i].bytes;
+      if (launches) launches[i] = p.stages[i].ntiles;
+    }
+  });
+}
+
+vie_status vie_entries(vie_op* h, const int32_t* rows, const int32_t* cols, int64_t count, void* out, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h && (count == 0 || (rows && cols && out)), VIE_EINVAL, "null argument");
+    VIE_REQUIRE(count >= 0, VIE_EINVAL, "negative count");
+    entries_pairs(h->geo, rows, cols, count, (double2*)out, (cudaStream_t)stream);
+  });
+}
+
+vie_status vie_rhs_planewave(vie_op* h, const double* khat, const double* pol, int64_t nrhs, void* V, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h && khat && pol && V && nrhs >= 1, VIE_EINVAL, "bad argument");
+    rhs_planewave(h->geo, khat, pol, (int)nrhs, (double2*)V, (cudaStream_t)stream);
+  });
+}
+
+vie_status vie_farfield(vie_op* h, const void* I, int64_t nrhs, const double* dirs, int64_t ndir, double* rcs,
+                        void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h && I && dirs && rcs && nrhs >= 1 && ndir >= 1, VIE_EINVAL, "bad argument");
+    farfield_impl(h->geo, h->tet_faces.as<int32_t>(), (const double2*)I, (int)nrhs, dirs, (int)ndir, rcs,
+                  (cudaStream_t)stream);
+  });
+}
+
+vie_status vie_mesh_faces(const vie_op* h, int32_t* faces, int32_t* tp, int32_t* tm) {
+  return guarded([&] {
+    VIE_REQUIRE(h, VIE_EINVAL, "null operator");
+    const int64_t n = h->mesh.nf;
+    if (faces) std::memcpy(faces, h->mesh.faces.data(), sizeof(int32_t) * 3 * n);
+    if (tp) std::memcpy(tp, h->mesh.tp.data(), sizeof(int32_t) * n);
+    if (tm) std::memcpy(tm, h->mesh.tm.data(), sizeof(int32_t) * n);
+  });
+}
+
+vie_status vie_mesh_host(const vie_voxels* body, int32_t leaf, int64_t* n, int32_t* faces, int32_t* tp, int32_t* tm,
+                         int32_t* perm, int32_t* levels) {
+  return guarded([&] {
+    VIE_REQUIRE(body && n, VIE_EINVAL, "null argument");
+    VIE_REQUIRE(body->nvox > 0 && body->ijk && body->eps && body->h > 0 && leaf >= 4, VIE_EINVAL, "invalid body");
+    Mesh m;
+    build_mesh(*body, m);
+    *n = m.nf;
+    if (faces) std::memcpy(faces, m.faces.data(), sizeof(int32_t) * 3 * m.nf);
+    if (tp) std::memcpy(tp, m.tp.data(), sizeof(int32_t) * m.nf);
+    if (tm) std::memcpy(tm, m.tm.data(), sizeof(int32_t) * m.nf);
+    if (perm || levels) {
+      std::vector<double> pts(3 * m.nf);
+      for (int64_t f = 0; f < m.nf; ++f)
+        for (int d = 0; d < 3; ++d) {
+          double a = double(m.vlat[3 * m.faces[3 * f] + d]) * m.h;
+          double b = double(m.vlat[3 * m.faces[3 * f + 1] + d]) * m.h;
+          double c = double(m.vlat[3 * m.faces[3 * f + 2] + d]) * m.h;
+          pts[3 * f + d] = ((a + b) + c) / 3.0;
+        }
+      Tree t;
+      build_tree(pts, leaf, t);
+      if (perm) std::memcpy(perm, t.perm.data(), sizeof(int32_t) * m.nf);
+      if (levels) *levels = t.levels;
+    }
+  });
+}
+
+vie_status vie_tree_perm(const vie_op* h, int32_t* perm) {
+  return guarded([&] {
+    VIE_REQUIRE(h && perm, VIE_EINVAL, "null argument");
+    std::memcpy(perm, h->tree.perm.data(), sizeof(int32_t) * h->mesh.nf);
+  });
+}
+
+vie_status vie_stats(const vie_op* h, vie_stats_t* out) {
+  return guarded([&] {
+    VIE_REQUIRE(h && out, VIE_EINVAL, "null argument");
+    *out = h->stats;
+  });
+}
+
+vie_status vie_solve(vie_op* h, const void* V, void* I, int64_t nrhs, double rtol, int32_t restart, int32_t max_iter,
+                     int32_t* iters, double* relres, void* stream) {
+  bool conv = true;
+  vie_status st = guarded([&] {
+    VIE_REQUIRE(h && V && I && nrhs >= 1, VIE_EINVAL, "bad argument");
+    VIE_REQUIRE(rtol > 0 && restart >= 1 && max_iter >= 1, VIE_EINVAL, "bad tolerance or iteration limits");
+    solve_gmres(h, (const double2*)V, (double2*)I, nrhs, rtol, restart, max_iter, iters, relres,
+                (cudaStream_t)stream, conv);
+  });
+  if (st == VIE_OK && !conv) {
+    set_error("GMRES stopped before reaching rtol");
+    return VIE_ENOTCONV;
+  }
+  return st;
+}
+
+}  // extern "C"

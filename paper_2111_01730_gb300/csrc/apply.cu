@@ -1,0 +1,297 @@
+// HOD-BF apply: batched block-sparse complex products, one launch per stage.
+//
+// A HOD-BF operator (Sec. III-A, Fig. 1) applied to x in cluster-tree order is
+//   y_tau = D_tau x_tau + sum over levels of B_tau x_sibling,
+// and every butterfly B = B^L W^L ... W^1 V^0 (Eq. 9) is a chain of
+// block-diagonal factors whose blocks are small dense matrices of uneven
+// sizes (the butterfly ranks).  The apply therefore is a short sequence of
+// stages; stage k multiplies, for every butterfly at once, all its factor-k
+// blocks with slices of the previous stage's coefficient vectors.  All blocks
+// of a stage are independent, so one launch per stage streams that stage's
+// factor bytes once from HBM:
+//   * blocks are stored row-major, rows padded to 16 bytes, in one buffer per stage;
+//   * work is cut into warp tiles of rows of one block; g lanes (a power of two)
+//     share a row, each lane streaming 16-byte vectors (two c64 or one c128
+//     entries) with coalesced loads; the g partial sums meet by warp shuffles
+//     and one lane writes the output (no atomics: every output row belongs to
+//     exactly one tile per stage, so results are deterministic);
+//   * coefficient vectors (small, L2 resident) are read through the read-only path.
+#include "internal.h"
+
+namespace vie {
+
+template <class T> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+
+template <class TV>
+__device__ __forceinline__ typename C2<TV>::type ldv(const typename C2<TV>::type* p) { return __ldg(p); }
+
+// Accumulate row . x for a row of K entries starting at A (row-major), lanes li..g.
+template <class TM, class TV, int NR>
+__device__ __forceinline__ void row_dot(const typename C2<TM>::type* __restrict__ A, int K, int li, int g,
+                                        const typename C2<TV>::type* __restrict__ x, int nrhs,
+                                        TV (&acc_re)[NR], TV (&acc_im)[NR]);
+
+template <>
+__device__ __forceinline__ void row_dot<float, float, 1>(const float2* __restrict__ A, int K, int li, int g,
+                                                          const float2* __restrict__ x, int nrhs,
+                                                          float (&re)[1], float (&im)[1]) {
+  const float4* A4 = reinterpret_cast<const float4*>(A);
+  for (int k = 2 * li; k < K; k += 2 * g) {
+    float4 a = __ldcs(A4 + (k >> 1));
+    float2 x0 = __ldg(x + k);
+    float2 x1 = (k + 1 < K) ? __ldg(x + k + 1) : make_float2(0.f, 0.f);
+    re[0] = fmaf(a.x, x0.x, re[0]); re[0] = fmaf(-a.y, x0.y, re[0]);
+    im[0] = fmaf(a.x, x0.y, im[0]); im[0] = fmaf(a.y, x0.x, im[0]);
+    re[0] = fmaf(a.z, x1.x, re[0]); re[0] = fmaf(-a.w, x1.y, re[0]);
+    im[0] = fmaf(a.z, x1.y, im[0]); im[0] = fmaf(a.w, x1.x, im[0]);
+  }
+}
+
+template <int NR>
+__device__ __forceinline__ void row_dot_c64_multi(const float2* __restrict__ A, int K, int li, int g,
+                                                  const float2* __restrict__ x, int nrhs, float (&re)[NR],
+                                                  float (&im)[NR]) {
+  const float4* A4 = reinterpret_cast<const float4*>(A);
+  for (int k = 2 * li; k < K; k += 2 * g) {
+    float4 a = __ldcs(A4 + (k >> 1));
+    const float2* x0 = x + (int64_t)k * nrhs;
+    const bool two = k + 1 < K;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      float2 u = __ldg(x0 + j);
+      float2 v = two ? __ldg(x0 + nrhs + j) : make_float2(0.f, 0.f);
+      re[j] = fmaf(a.x, u.x, re[j]); re[j] = fmaf(-a.y, u.y, re[j]);
+      im[j] = fmaf(a.x, u.y, im[j]); im[j] = fmaf(a.y, u.x, im[j]);
+      re[j] = fmaf(a.z, v.x, re[j]); re[j] = fmaf(-a.w, v.y, re[j]);
+      im[j] = fmaf(a.z, v.y, im[j]); im[j] = fmaf(a.w, v.x, im[j]);
+    }
+  }
+}
+
+// generic (any factor / vector precision, any rhs chunk): one complex entry per step
+template <class TM, class TV, int NR>
+__device__ __forceinline__ void row_dot_generic(const typename C2<TM>::type* __restrict__ A, int K, int li, int g,
+                                                const typename C2<TV>::type* __restrict__ x, int nrhs,
+                                                TV (&re)[NR], TV (&im)[NR]) {
+  for (int k = li; k < K; k += g) {
+    typename C2<TM>::type a = A[k];
+    const TV ar = TV(a.x), ai = TV(a.y);
+    const typename C2<TV>::type* xk = x + (int64_t)k * nrhs;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      typename C2<TV>::type u = __ldg(xk + j);
+      re[j] += ar * u.x - ai * u.y;
+      im[j] += ar * u.y + ai * u.x;
+    }
+  }
+}
+
+template <class TM, class TV, int NR>
+__global__ void __launch_bounds__(256) stage_kernel(const OpDesc* __restrict__ ops, const Tile* __restrict__ tiles,
+                                                    int64_t ntiles, const typename C2<TM>::type* __restrict__ mats,
+                                                    const typename C2<TV>::type* xt, typename C2<TV>::type* yt,
+                                                    typename C2<TV>::type* coef, int nrhs, int rhs0) {
+  using V2 = typename C2<TV>::type;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp0; t < ntiles; t += nwarps) {
+    const Tile tl = tiles[t];
+    const OpDesc op = ops[tl.op];
+    const int g = tl.g, rp = 32 / g;
+    const int li = lane & (g - 1);
+    const V2* xin = (op.in_space == SP_X ? xt : coef) + op.in_off * nrhs + rhs0;
+    V2* yout = (op.out_space == SP_Y ? yt : coef) + op.out_off * nrhs + rhs0;
+    for (int r = tl.r0 + lane / g; r < tl.r0 + tl.nr; r += rp) {
+      const bool active = r < op.M;
+      TV re[NR], im[NR];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) { re[j] = TV(0); im[j] = TV(0); }
+      if (active) {
+        const typename C2<TM>::type* A = mats + op.mat_off + (int64_t)r * op.ld;
+        if constexpr (sizeof(TM) == 4 && sizeof(TV) == 4) {
+          if constexpr (NR == 1) {
+            if (nrhs == 1) row_dot<float, float, 1>(A, op.K, li, g, xin, nrhs, re, im);
+            else row_dot_c64_multi<1>(A, op.K, li, g, xin, nrhs, re, im);
+          } else {
+            row_dot_c64_multi<NR>(A, op.K, li, g, xin, nrhs, re, im);
+          }
+        } else {
+          row_dot_generic<TM, TV, NR>(A, op.K, li, g, xin, nrhs, re, im);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+        for (int o = g >> 1; o > 0; o >>= 1) {
+          re[j] += __shfl_xor_sync(0xffffffffu, re[j], o);
+          im[j] += __shfl_xor_sync(0xffffffffu, im[j], o);
+        }
+      if (active && li == 0) {
+        V2* yr = yout + (int64_t)r * nrhs;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          if (op.accumulate) {
+            V2 v = yr[j];
+            v.x += re[j];
+            v.y += im[j];
+            yr[j] = v;
+          } else {
+            V2 v;
+            v.x = re[j];
+            v.y = im[j];
+            yr[j] = v;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// permutation gather / scatter (cluster-tree order <-> original face order)
+// ---------------------------------------------------------------------------
+template <class TV>
+__global__ void gather_kernel(const int32_t* perm, int64_t n, int nrhs, const typename C2<TV>::type* X, int64_t ldx,
+                              typename C2<TV>::type* xt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / nrhs;
+    int j = int(e % nrhs);
+    xt[e] = X[perm[i] + (int64_t)j * ldx];
+  }
+}
+
+template <class TV>
+__global__ void scatter_kernel(const int32_t* perm, int64_t n, int nrhs, const typename C2<TV>::type* yt,
+                               typename C2<TV>::type* Y, int64_t ldy) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / nrhs;
+    int j = int(e % nrhs);
+    Y[perm[i] + (int64_t)j * ldy] = yt[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// matrix packing: c128 source (row- or column-major) -> row-major padded c64/c128
+// ---------------------------------------------------------------------------
+template <class TM>
+__global__ void pack_kernel(const double2* src, const int64_t* src_off, const int32_t* src_ld, const int32_t* colmajor,
+                            const int64_t* dst_off, const int32_t* M, const int32_t* K, const int32_t* ld,
+                            typename C2<TM>::type* dst) {
+  const int i = blockIdx.x;
+  const int m = M[i], k = K[i], l = ld[i], sl = src_ld[i];
+  const bool cm = colmajor[i] != 0;
+  const double2* s = src + src_off[i];
+  typename C2<TM>::type* d = dst + dst_off[i];
+  for (int64_t e = threadIdx.x; e < (int64_t)m * l; e += blockDim.x) {
+    int r = int(e / l), c = int(e % l);
+    double2 v = make_double2(0.0, 0.0);
+    if (c < k) v = cm ? s[r + (int64_t)c * sl] : s[(int64_t)r * sl + c];
+    typename C2<TM>::type o;
+    o.x = TM(v.x);
+    o.y = TM(v.y);
+    d[e] = o;
+  }
+}
+
+void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* d_src_ld, const int32_t* d_src_colmajor,
+                   const int64_t* d_dst_off, const int32_t* d_M, const int32_t* d_K, const int32_t* d_ld, int nmat,
+                   void* dst, int dst_dtype, cudaStream_t s) {
+  if (nmat <= 0) return;
+  if (dst_dtype == VIE_C64)
+    pack_kernel<float><<<nmat, 256, 0, s>>>(src, d_src_off, d_src_ld, d_src_colmajor, d_dst_off, d_M, d_K, d_ld,
+                                            static_cast<float2*>(dst));
+  else
+    pack_kernel<double><<<nmat, 256, 0, s>>>(src, d_src_off, d_src_ld, d_src_colmajor, d_dst_off, d_M, d_K, d_ld,
+                                             static_cast<double2*>(dst));
+  VIE_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// tiles: rows of one op per warp tile, about 16 KB of factor data per tile
+// ---------------------------------------------------------------------------
+void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles) {
+  tiles.clear();
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const OpDesc& o = ops[i];
+    if (o.M <= 0) continue;
+    int per = (o.K + 1) / 2;  // 16-byte vectors per row for c64
+    int g = 1;
+    while (g < 32 && g < per) g <<= 1;
+    int rp = 32 / g;
+    int64_t row_bytes = (int64_t)o.ld * 8;
+    int64_t passes = std::max<int64_t>(1, 16384 / std::max<int64_t>(1, row_bytes * rp));
+    int nr = int(std::min<int64_t>(passes * rp, (int64_t)((o.M + rp - 1) / rp) * rp));
+    for (int r0 = 0; r0 < o.M; r0 += nr) tiles.push_back(Tile{int32_t(i), r0, std::min(nr, o.M - r0 + (rp - 1)) / rp * rp, g});
+  }
+}
+
+template <class TM, class TV>
+static void launch_stage(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, cudaStream_t s) {
+  using V2 = typename C2<TV>::type;
+  if (st.ntiles == 0) return;
+  int64_t blocks = (st.ntiles + 7) / 8;
+  int grid = (int)std::min<int64_t>(blocks, 152 * 16);
+  const OpDesc* ops = st.ops.as<OpDesc>();
+  const Tile* tiles = st.tiles.as<Tile>();
+  const typename C2<TM>::type* mats = st.mats.as<typename C2<TM>::type>();
+  for (int r0 = 0; r0 < nrhs;) {
+    int left = nrhs - r0;
+    if (left >= 8) {
+      stage_kernel<TM, TV, 8><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      r0 += 8;
+    } else if (left >= 4) {
+      stage_kernel<TM, TV, 4><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      r0 += 4;
+    } else if (left >= 2) {
+      stage_kernel<TM, TV, 2><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      r0 += 2;
+    } else {
+      stage_kernel<TM, TV, 1><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      r0 += 1;
+    }
+    VIE_CUDA(cudaGetLastError());
+  }
+}
+
+template <class TV>
+static void run_program(const Program& p, const int32_t* perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
+                        int64_t ldy, void* xt, void* yt, void* coef, cudaStream_t s, cudaEvent_t* ev) {
+  using V2 = typename C2<TV>::type;
+  const int64_t tot = p.n * nrhs;
+  const int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
+  int e = 0;
+  if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+  gather_kernel<TV><<<grid, 256, 0, s>>>(perm, p.n, (int)nrhs, (const V2*)X, ldx, (V2*)xt);
+  VIE_CUDA(cudaGetLastError());
+  if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+  for (const Stage& st : p.stages) {
+    if (p.factor_dtype == VIE_C64) launch_stage<float, TV>(st, xt, yt, coef, (int)nrhs, s);
+    else launch_stage<double, TV>(st, xt, yt, coef, (int)nrhs, s);
+    if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+  }
+  scatter_kernel<TV><<<grid, 256, 0, s>>>(perm, p.n, (int)nrhs, (const V2*)yt, (V2*)Y, ldy);
+  VIE_CUDA(cudaGetLastError());
+  if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+}
+
+void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
+                   int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s, cudaEvent_t* ev) {
+  if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
+  else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
+}
+
+int64_t program_launches(const Program& p, int64_t nrhs) {
+  int64_t chunks = 0;
+  for (int64_t r = 0; r < nrhs;) {
+    int64_t left = nrhs - r;
+    r += left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
+    ++chunks;
+  }
+  int64_t n = 2;
+  for (const Stage& st : p.stages) n += st.ntiles ? chunks : 0;
+  return n;
+}
+
+}  // namespace vie

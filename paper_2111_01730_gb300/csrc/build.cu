@@ -1,0 +1,477 @@
+// HOD-BF construction on the GPU (Sec. III-A, Eqs. 7-10).
+//
+// Every off-diagonal block B_tau (tau at tree level l, L = L_H - l butterfly
+// levels, o = tau, s = its sibling) is built level by level, and level k of
+// all butterflies of all tree levels runs as one batch:
+//   k = 0   : ID of Z(o_sample, nu) for every leaf nu of T_s   -> V^0, skeletons
+//   k >= 1  : ID of Z(tau_sample, [nu1_bar, nu2_bar]) for tau at level k of T_o
+//             and nu at level L - k of T_s (Eq. 8)              -> W^k, skeletons
+//   final   : B^L = Z(tau_leaf, s_bar) for the leaves of T_o (Eq. 9)
+// Each batch: host builds row samples and column lists -> GPU evaluates the
+// entries (entries.cu) -> GPU batched ID (id.cu) -> host reads ranks and
+// pivots -> GPU packs the factors into the stage buffers of the apply program.
+//
+// Row sampling (the paper does not say how rows are chosen for the IDs): for
+// a candidate column set J of size c, the c + 4 rows of tau nearest to the
+// bounding box of nu plus c/2 + oversample rows drawn uniformly at random
+// without replacement (seeded); all rows when tau has no more than that.  The
+// near rows carry the strong near-field couplings that set the rank of
+// touching blocks; uniform rows alone miss them.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+
+#include "internal.h"
+
+namespace vie {
+
+namespace {
+
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct Sampler {
+  const Tree& t;
+  const std::vector<double>& pts;  // original order, 3n
+  int LH;
+  uint64_t seed;
+  int oversample;
+
+  double box_pt(const double* bb, const double* p) const {
+    double s = 0;
+    for (int d = 0; d < 3; ++d) {
+      double e = std::max({0.0, bb[d] - p[d], p[d] - bb[3 + d]});
+      s += e * e;
+    }
+    return s;
+  }
+  double box_box(const double* a, const double* b) const {
+    double s = 0;
+    for (int d = 0; d < 3; ++d) {
+      double e = std::max({0.0, a[d] - b[3 + d], b[d] - a[3 + d]});
+      s += e * e;
+    }
+    return s;
+  }
+
+  // k nearest tree positions of node (lev, idx) to the box `bb` (ties: lower position)
+  void nearest(int lev, int64_t idx, const double* bb, int k, std::vector<int64_t>& out) const {
+    out.clear();
+    if (k <= 0) return;
+    using Item = std::pair<double, std::pair<int, int64_t>>;  // (dist, (level, node))
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+    std::priority_queue<std::pair<double, int64_t>> best;  // max-heap of (dist, pos)
+    pq.push({box_box(&t.bbox[lev][6 * idx], bb), {lev, idx}});
+    while (!pq.empty()) {
+      Item it = pq.top();
+      pq.pop();
+      if ((int)best.size() == k && it.first > best.top().first) break;
+      int l = it.second.first;
+      int64_t i = it.second.second;
+      if (l == LH) {
+        for (int64_t p = t.bounds[l][i]; p < t.bounds[l][i + 1]; ++p) {
+          double d = box_pt(bb, &pts[3 * t.perm[p]]);
+          std::pair<double, int64_t> e{d, p};
+          if ((int)best.size() < k) best.push(e);
+          else if (e < best.top()) { best.pop(); best.push(e); }
+        }
+      } else {
+        for (int c = 0; c < 2; ++c) {
+          int64_t ch = 2 * i + c;
+          pq.push({box_box(&t.bbox[l + 1][6 * ch], bb), {l + 1, ch}});
+        }
+      }
+    }
+    while (!best.empty()) { out.push_back(best.top().second); best.pop(); }
+  }
+
+  // rows (tree positions, sorted) for the ID of Z(tau, J): tau = (lev, idx), nu = (nlev, nidx)
+  void rows(int lev, int64_t idx, int nlev, int64_t nidx, int ncand, uint64_t key, std::vector<int32_t>& out) const {
+    const int64_t a = t.bounds[lev][idx], b = t.bounds[lev][idx + 1];
+    const int64_t sz = b - a;
+    const int nnear = ncand + 4, nrand = ncand / 2 + oversample;
+    out.clear();
+    if (sz <= nnear + nrand) {
+      for (int64_t p = a; p < b; ++p) out.push_back((int32_t)p);
+      return;
+    }
+    std::vector<int64_t> nb;
+    nearest(lev, idx, &t.bbox[nlev][6 * nidx], nnear, nb);
+    std::vector<int64_t> pick(nb);
+    uint64_t s = seed ^ (key * 0xD1B54A32D192ED03ull);
+    // Floyd's algorithm: nrand distinct positions in [0, sz)
+    std::vector<int64_t> chosen;
+    chosen.reserve(nrand);
+    for (int64_t j = sz - nrand; j < sz; ++j) {
+      int64_t r = (int64_t)(splitmix(s) % (uint64_t)(j + 1));
+      bool dup = std::find(chosen.begin(), chosen.end(), r) != chosen.end();
+      chosen.push_back(dup ? j : r);
+    }
+    for (int64_t c : chosen) pick.push_back(a + c);
+    std::sort(pick.begin(), pick.end());
+    pick.erase(std::unique(pick.begin(), pick.end()), pick.end());
+    for (int64_t p : pick) out.push_back((int32_t)p);
+  }
+};
+
+struct BF {
+  int l;
+  int64_t i;
+  int L;
+  std::vector<std::vector<int32_t>> rank;            // rank[k][blk]
+  std::vector<std::vector<int64_t>> coff;            // coefficient offsets
+  std::vector<std::vector<std::vector<int32_t>>> skel;  // skeleton tree positions (last level only kept)
+};
+
+// one matrix to evaluate (+ optionally decompose) in a batch
+struct Job {
+  int bf;          // butterfly index, -1 for a leaf D block
+  int k;           // butterfly level (ID level), or L + 1 for a B block
+  int64_t blk;     // block index within the level
+  bool id;         // run the ID
+  std::vector<int32_t> rows, cols;  // tree positions
+};
+
+}  // namespace
+
+static void finalize_stage(Stage& st, const std::vector<OpDesc>& ops, std::vector<DevBuf>& chunks,
+                           const std::vector<int64_t>& chunk_elems, int elem_bytes, cudaStream_t s) {
+  int64_t tot = 0;
+  for (auto e : chunk_elems) tot += e;
+  st.mats.alloc(std::max<int64_t>(tot, 2) * elem_bytes);
+  int64_t off = 0;
+  for (size_t c = 0; c < chunks.size(); ++c) {
+    if (chunk_elems[c])
+      VIE_CUDA(cudaMemcpyAsync((char*)st.mats.p + off * elem_bytes, chunks[c].p, chunk_elems[c] * elem_bytes,
+                               cudaMemcpyDeviceToDevice, s));
+    off += chunk_elems[c];
+  }
+  std::vector<Tile> tiles;
+  make_tiles(ops, tiles);
+  st.nops = (int64_t)ops.size();
+  st.ntiles = (int64_t)tiles.size();
+  st.ops.alloc(sizeof(OpDesc) * std::max<size_t>(1, ops.size()));
+  st.tiles.alloc(sizeof(Tile) * std::max<size_t>(1, tiles.size()));
+  if (!ops.empty()) VIE_CUDA(cudaMemcpyAsync(st.ops.p, ops.data(), sizeof(OpDesc) * ops.size(), cudaMemcpyHostToDevice, s));
+  if (!tiles.empty())
+    VIE_CUDA(cudaMemcpyAsync(st.tiles.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
+  st.entries = 0;
+  for (auto& o : ops) st.entries += (int64_t)o.M * o.K;
+  st.bytes = tot * elem_bytes;
+  VIE_CUDA(cudaStreamSynchronize(s));
+  for (auto& c : chunks) c.release();
+  chunks.clear();
+}
+
+void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
+  const Tree& t = h->tree;
+  const int LH = t.levels;
+  const int64_t N = h->mesh.nf;
+  const vie_config& cfg = h->cfg;
+  const int elem_bytes = cfg.factor_dtype == VIE_C64 ? 8 : 16;
+  // face centroids (original order), same arithmetic as the tree
+  std::vector<double> pts(3 * N);
+  for (int64_t f = 0; f < N; ++f)
+    for (int d = 0; d < 3; ++d) {
+      double a = double(h->mesh.vlat[3 * h->mesh.faces[3 * f] + d]) * h->mesh.h;
+      double b = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 1] + d]) * h->mesh.h;
+      double c = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 2] + d]) * h->mesh.h;
+      pts[3 * f + d] = ((a + b) + c) / 3.0;
+    }
+  Sampler smp{t, pts, LH, cfg.seed, cfg.oversample};
+  // butterflies
+  std::vector<BF> bfs;
+  for (int l = 1; l <= LH; ++l)
+    for (int64_t i = 0; i < (int64_t(1) << l); ++i) {
+      BF b;
+      b.l = l; b.i = i; b.L = LH - l;
+      b.rank.resize(b.L + 1);
+      b.coff.resize(b.L + 1);
+      bfs.push_back(std::move(b));
+    }
+  Program& P = h->z;
+  P.n = N;
+  P.factor_dtype = cfg.factor_dtype;
+  const int nstages = LH + 1;  // stage k: V^0/D (k = 0), W^k and B of L = k - 1
+  P.stages.clear();
+  P.stages.resize(nstages);
+  int64_t coef_next = 0;
+  const size_t budget = size_t(8) << 30;  // bytes of c128 scratch per chunk
+
+  for (int k = 0; k < nstages; ++k) {
+    // ---- collect the jobs of this batch ----
+    std::vector<Job> jobs;
+    if (k == 0)
+      for (int64_t i = 0; i < (int64_t(1) << LH); ++i) {
+        Job j{-1, 0, i, false, {}, {}};
+        for (int64_t p = t.bounds[LH][i]; p < t.bounds[LH][i + 1]; ++p) { j.rows.push_back((int32_t)p); }
+        j.cols = j.rows;
+        jobs.push_back(std::move(j));
+      }
+    for (int b = 0; b < (int)bfs.size(); ++b) {
+      BF& B = bfs[b];
+      const int lo = B.l, L = B.L;
+      const int64_t so = B.i ^ 1;
+      if (k <= L) {
+        const int64_t ntau = int64_t(1) << k, nnu = int64_t(1) << (L - k);
+        for (int64_t ti = 0; ti < ntau; ++ti)
+          for (int64_t nj = 0; nj < nnu; ++nj) {
+            Job j{b, k, ti * nnu + nj, true, {}, {}};
+            const int nlev = lo + L - k;  // global level of nu
+            const int64_t nidx = so * nnu + nj;
+            if (k == 0) {
+              for (int64_t p = t.bounds[nlev][nidx]; p < t.bounds[nlev][nidx + 1]; ++p) j.cols.push_back((int32_t)p);
+            } else {
+              const int64_t pnnu = nnu * 2, pt = ti / 2;
+              const auto& s1 = B.skel[0][pt * pnnu + 2 * nj];
+              const auto& s2 = B.skel[0][pt * pnnu + 2 * nj + 1];
+              j.cols.insert(j.cols.end(), s1.begin(), s1.end());
+              j.cols.insert(j.cols.end(), s2.begin(), s2.end());
+            }
+            jobs.push_back(std::move(j));
+          }
+      } else if (k == L + 1) {
+        const int64_t ntau = int64_t(1) << L;
+        for (int64_t ti = 0; ti < ntau; ++ti) {
+          Job j{b, k, ti, false, {}, {}};
+          const int64_t gi = B.i * ntau + ti;
+          for (int64_t p = t.bounds[LH][gi]; p < t.bounds[LH][gi + 1]; ++p) j.rows.push_back((int32_t)p);
+          j.cols = B.skel[0][ti];
+          jobs.push_back(std::move(j));
+        }
+      }
+    }
+    // row samples of the ID jobs (independent per job, deterministic per seed)
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < (int64_t)jobs.size(); ++q) {
+      Job& j = jobs[q];
+      if (!j.id) continue;
+      const BF& B = bfs[j.bf];
+      const int64_t nnu = int64_t(1) << (B.L - j.k);
+      const int64_t ti = j.blk / nnu, nj = j.blk % nnu;
+      const int tlev = B.l + j.k;
+      const int64_t tidx = B.i * (int64_t(1) << j.k) + ti;
+      const int nlev = B.l + B.L - j.k;
+      const int64_t nidx = (B.i ^ 1) * nnu + nj;
+      uint64_t key = ((uint64_t)j.bf << 40) ^ ((uint64_t)j.k << 32) ^ (uint64_t)j.blk;
+      smp.rows(tlev, tidx, nlev, nidx, (int)j.cols.size(), key, j.rows);
+    }
+    // ---- process in chunks ----
+    std::vector<OpDesc> ops;
+    std::vector<DevBuf> chunks;
+    std::vector<int64_t> chunk_elems;
+    int64_t stage_off = 0;
+    std::vector<std::vector<int32_t>> new_rank(bfs.size());
+    for (size_t b = 0; b < bfs.size(); ++b)
+      if (k <= bfs[b].L) new_rank[b].assign(size_t(1) << k << (bfs[b].L - k), 0);
+    std::vector<std::vector<std::vector<int32_t>>> new_skel(bfs.size());
+    for (size_t b = 0; b < bfs.size(); ++b)
+      if (k <= bfs[b].L) new_skel[b].resize(size_t(1) << bfs[b].L);
+    size_t q0 = 0;
+    while (q0 < jobs.size()) {
+      size_t q1 = q0, bytes = 0;
+      while (q1 < jobs.size()) {
+        size_t e = (size_t)jobs[q1].rows.size() * jobs[q1].cols.size() * 16;
+        if (q1 > q0 && bytes + 2 * e > budget) break;
+        bytes += 2 * e;
+        ++q1;
+      }
+      const int nj = int(q1 - q0);
+      // index pools and blocks
+      std::vector<int32_t> rows, cols;
+      std::vector<EntryBlock> eb(nj);
+      std::vector<int64_t> prefix(nj);
+      int64_t aoff = 0;
+      for (int q = 0; q < nj; ++q) {
+        Job& j = jobs[q0 + q];
+        eb[q] = EntryBlock{aoff, (int64_t)rows.size(), (int64_t)cols.size(), (int32_t)j.rows.size(), (int32_t)j.cols.size()};
+        prefix[q] = aoff;
+        for (int32_t p : j.rows) rows.push_back(t.perm[p]);
+        for (int32_t p : j.cols) cols.push_back(t.perm[p]);
+        aoff += (int64_t)j.rows.size() * j.cols.size();
+      }
+      res.entries_evaluated += aoff;
+      DevBuf drows, dcols, deb, dpre, dA;
+      drows.alloc(sizeof(int32_t) * std::max<size_t>(1, rows.size()));
+      dcols.alloc(sizeof(int32_t) * std::max<size_t>(1, cols.size()));
+      deb.alloc(sizeof(EntryBlock) * nj);
+      dpre.alloc(sizeof(int64_t) * nj);
+      dA.alloc(sizeof(double2) * std::max<int64_t>(1, aoff));
+      VIE_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
+      VIE_CUDA(cudaMemcpyAsync(dcols.p, cols.data(), sizeof(int32_t) * cols.size(), cudaMemcpyHostToDevice, s));
+      VIE_CUDA(cudaMemcpyAsync(deb.p, eb.data(), sizeof(EntryBlock) * nj, cudaMemcpyHostToDevice, s));
+      VIE_CUDA(cudaMemcpyAsync(dpre.p, prefix.data(), sizeof(int64_t) * nj, cudaMemcpyHostToDevice, s));
+      entries_blocks(h->geo, deb.as<EntryBlock>(), dpre.as<int64_t>(), nj, aoff, drows.as<int32_t>(),
+                     dcols.as<int32_t>(), dA.as<double2>(), s);
+      // IDs
+      std::vector<IdJob> ij;
+      std::vector<int> ij_q;
+      int64_t voff = 0, poff = 0;
+      int maxn = 1;
+      for (int q = 0; q < nj; ++q) {
+        Job& j = jobs[q0 + q];
+        if (!j.id) continue;
+        const int m = (int)j.rows.size(), n = (int)j.cols.size();
+        ij.push_back(IdJob{eb[q].out_off, voff, poff, m, n});
+        ij_q.push_back(q);
+        voff += (int64_t)std::min(m, n) * n;
+        poff += n;
+        maxn = std::max(maxn, n);
+      }
+      DevBuf dij, dV, dpiv, drank;
+      std::vector<int32_t> piv(poff), rk(ij.size());
+      if (!ij.empty()) {
+        dij.alloc(sizeof(IdJob) * ij.size());
+        dV.alloc(sizeof(double2) * std::max<int64_t>(1, voff));
+        dpiv.alloc(sizeof(int32_t) * std::max<int64_t>(1, poff));
+        drank.alloc(sizeof(int32_t) * ij.size());
+        VIE_CUDA(cudaMemcpyAsync(dij.p, ij.data(), sizeof(IdJob) * ij.size(), cudaMemcpyHostToDevice, s));
+        id_batched(dij.as<IdJob>(), (int)ij.size(), maxn, dA.as<double2>(), dV.as<double2>(), dpiv.as<int32_t>(),
+                   drank.as<int32_t>(), cfg.tol_con, s);
+        VIE_CUDA(cudaMemcpyAsync(piv.data(), dpiv.p, sizeof(int32_t) * poff, cudaMemcpyDeviceToHost, s));
+        VIE_CUDA(cudaMemcpyAsync(rk.data(), drank.p, sizeof(int32_t) * ij.size(), cudaMemcpyDeviceToHost, s));
+        VIE_CUDA(cudaStreamSynchronize(s));
+      }
+      // record ranks / skeletons, build the ops and the pack list of this chunk
+      std::vector<int64_t> src_off, dst_off;
+      std::vector<int32_t> src_ld, colmaj, pM, pK, pld;
+      int64_t celems = 0;
+      auto add_pack = [&](int64_t so, int32_t sld, int32_t cm, int32_t M, int32_t K) -> int64_t {
+        int32_t ld = (K + 1) & ~1;
+        int64_t o = celems;
+        src_off.push_back(so); src_ld.push_back(sld); colmaj.push_back(cm);
+        dst_off.push_back(o); pM.push_back(M); pK.push_back(K); pld.push_back(ld);
+        celems += (int64_t)M * ld;
+        celems = (celems + 1) & ~int64_t(1);
+        return o;
+      };
+      int idc = 0;
+      for (int q = 0; q < nj; ++q) {
+        Job& j = jobs[q0 + q];
+        if (j.bf < 0) {  // leaf D block: y_tau = D_tau x_tau
+          const int m = (int)j.rows.size();
+          int64_t mo = add_pack(eb[q].out_off, m, 1, m, m);
+          OpDesc o{};
+          o.mat_off = stage_off + mo; o.M = m; o.K = m; o.ld = (m + 1) & ~1;
+          o.in_space = SP_X; o.in_off = j.rows[0]; o.out_space = SP_Y; o.out_off = j.rows[0]; o.accumulate = 0;
+          ops.push_back(o);
+          continue;
+        }
+        BF& B = bfs[j.bf];
+        if (!j.id) {  // B^L block of butterfly B: y_tau += Z(tau, s_bar) c
+          const int m = (int)j.rows.size(), n = (int)j.cols.size();
+          if (n == 0) continue;
+          int64_t mo = add_pack(eb[q].out_off, m, 1, m, n);
+          OpDesc o{};
+          o.mat_off = stage_off + mo; o.M = m; o.K = n; o.ld = (n + 1) & ~1;
+          o.in_space = SP_C; o.in_off = B.coff[B.L][j.blk]; o.out_space = SP_Y; o.out_off = j.rows[0];
+          o.accumulate = 1;
+          ops.push_back(o);
+          continue;
+        }
+        const IdJob& J = ij[idc];
+        const int r = rk[idc];
+        ++idc;
+        const int n = (int)j.cols.size();
+        new_rank[j.bf][j.blk] = r;
+        auto& sk = new_skel[j.bf][j.blk];
+        sk.resize(r);
+        for (int c = 0; c < r; ++c) sk[c] = j.cols[piv[J.p_off + c]];
+        res.max_rank = std::max(res.max_rank, r);
+        if (r == 0) continue;
+        int64_t mo = add_pack(J.v_off, n, 0, r, n);
+        OpDesc o{};
+        o.mat_off = stage_off + mo; o.M = r; o.K = n; o.ld = (n + 1) & ~1;
+        o.out_space = SP_C;
+        o.out_off = -1;  // assigned below once all ranks of the level are known
+        o.accumulate = 0;
+        const int64_t nnu = int64_t(1) << (B.L - j.k);
+        if (j.k == 0) {
+          o.in_space = SP_X;
+          o.in_off = j.cols[0];  // the leaf nu is a contiguous range of tree positions
+        } else {
+          o.in_space = SP_C;
+          const int64_t ti = j.blk / nnu, nj2 = j.blk % nnu, pnnu = nnu * 2;
+          o.in_off = B.coff[j.k - 1][(ti / 2) * pnnu + 2 * nj2];
+        }
+        o.pad = j.bf;
+        o.K = n;
+        ops.push_back(o);
+        // remember the block for the coefficient offset
+        ops.back().out_off = -(int64_t)(j.blk + 1);
+      }
+      // pack this chunk
+      DevBuf dst;
+      dst.alloc(std::max<int64_t>(celems, 2) * elem_bytes);
+      if (!src_off.empty()) {
+        const int nm = (int)src_off.size();
+        // source pools: ID outputs (row-major) live in dV, entry blocks (col-major) in dA
+        // -> pack in two launches
+        std::vector<int> from_v(nm);
+        for (int i = 0; i < nm; ++i) from_v[i] = colmaj[i] == 0;
+        auto launch = [&](bool fromV) {
+          std::vector<int64_t> so, dofs;
+          std::vector<int32_t> sl, cm, M, K, L;
+          for (int i = 0; i < nm; ++i)
+            if ((bool)from_v[i] == fromV) {
+              so.push_back(src_off[i]); sl.push_back(src_ld[i]); cm.push_back(colmaj[i]);
+              dofs.push_back(dst_off[i]); M.push_back(pM[i]); K.push_back(pK[i]); L.push_back(pld[i]);
+            }
+          const int c = (int)so.size();
+          if (!c) return;
+          DevBuf b1, b2, b3, b4, b5, b6, b7;
+          b1.alloc(8 * c); b2.alloc(4 * c); b3.alloc(4 * c); b4.alloc(8 * c); b5.alloc(4 * c); b6.alloc(4 * c); b7.alloc(4 * c);
+          VIE_CUDA(cudaMemcpyAsync(b1.p, so.data(), 8 * c, cudaMemcpyHostToDevice, s));
+          VIE_CUDA(cudaMemcpyAsync(b2.p, sl.data(), 4 * c, cudaMemcpyHostToDevice, s));
+          VIE_CUDA(cudaMemcpyAsync(b3.p, cm.data(), 4 * c, cudaMemcpyHostToDevice, s));
+          VIE_CUDA(cudaMemcpyAsync(b4.p, dofs.data(), 8 * c, cudaMemcpyHostToDevice, s));
+          VIE_CUDA(cudaMemcpyAsync(b5.p, M.data(), 4 * c, cudaMemcpyHostToDevice, s));
+          VIE_CUDA(cudaMemcpyAsync(b6.p, K.data(), 4 * c, cudaMemcpyHostToDevice, s));
+          VIE_CUDA(cudaMemcpyAsync(b7.p, L.data(), 4 * c, cudaMemcpyHostToDevice, s));
+          pack_matrices(fromV ? dV.as<double2>() : dA.as<double2>(), b1.as<int64_t>(), b2.as<int32_t>(),
+                        b3.as<int32_t>(), b4.as<int64_t>(), b5.as<int32_t>(), b6.as<int32_t>(), b7.as<int32_t>(), c,
+                        dst.p, cfg.factor_dtype, s);
+          VIE_CUDA(cudaStreamSynchronize(s));
+        };
+        launch(true);
+        launch(false);
+      }
+      stage_off += celems;
+      chunks.push_back(std::move(dst));
+      chunk_elems.push_back(celems);
+      q0 = q1;
+    }
+    // coefficient offsets of this level, in block order per butterfly
+    for (size_t b = 0; b < bfs.size(); ++b) {
+      BF& B = bfs[b];
+      if (k > B.L) continue;
+      B.rank[k] = new_rank[b];
+      B.coff[k].resize(B.rank[k].size());
+      for (size_t blk = 0; blk < B.rank[k].size(); ++blk) {
+        B.coff[k][blk] = coef_next;
+        coef_next += B.rank[k][blk];
+      }
+      B.skel.assign(1, std::move(new_skel[b]));
+    }
+    for (auto& o : ops)
+      if (o.out_space == SP_C && o.out_off < 0) {
+        int64_t blk = -o.out_off - 1;
+        o.out_off = bfs[o.pad].coff[k][blk];
+        o.pad = 0;
+      }
+    finalize_stage(P.stages[k], ops, chunks, chunk_elems, elem_bytes, s);
+  }
+  P.ncoef = coef_next;
+  P.entries = 0;
+  P.bytes = 0;
+  for (auto& st : P.stages) { P.entries += st.entries; P.bytes += st.bytes; }
+}
+
+}  // namespace vie

@@ -1,0 +1,184 @@
+// Batched interpolative decomposition (Eq. 7) by column-pivoted Householder QR, FP64.
+//
+// For each job, the m x n column-major block A (complex) is factored as
+// A P = Q R with Businger-Golub column pivoting; the rank r is the number of
+// pivots with |R_kk| > tol |R_11| (reading of "O(chi_con)").  The output is the
+// pivot order (the first r entries are the skeleton columns) and the
+// interpolation matrix V = [I, R11^-1 R12] P^T (r x n, row-major), so that
+// A ~ A(:, skeleton) V.
+//
+// One CTA per job.  Column norms are downdated after every reflection and
+// recomputed from the remaining rows when cancellation has eaten most of them.
+#include "internal.h"
+
+namespace vie {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) id_kernel(const IdJob* jobs, double2* Apool, double2* Vpool, int32_t* pivpool,
+                                                int32_t* rank_out, double tol) {
+  extern __shared__ double smem[];
+  const IdJob J = jobs[blockIdx.x];
+  const int m = J.m, n = J.n;
+  const int kmax = min(m, n);
+  double* cn = smem;                       // n
+  double* cref = cn + n;                   // n
+  double2* rd = reinterpret_cast<double2*>(cref + n);  // kmax
+  int* pv = reinterpret_cast<int*>(rd + kmax);         // n
+  __shared__ double s_wv[NT / 32];
+  __shared__ int s_wi[NT / 32];
+  __shared__ double s_nrm, s_vn2;
+  __shared__ int s_p;
+  __shared__ double2 s_v0;
+  double2* a = Apool + J.a_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+
+  for (int j = warp; j < n; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) s += abs2(a[i + (int64_t)j * m]);
+    s = warp_sum(s);
+    if (lane == 0) { cn[j] = s; cref[j] = s; pv[j] = j; }
+  }
+  __syncthreads();
+  int r = kmax;
+  double R00 = 0.0;
+  for (int i = 0; i < kmax; ++i) {
+    // pivot: largest remaining column norm (ties: lowest index)
+    double bv = -1.0;
+    int bi = n;
+    for (int j = i + tid; j < n; j += NT)
+      if (cn[j] > bv) { bv = cn[j]; bi = j; }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_wv[warp] = bv; s_wi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = s_wv[0];
+      int k = s_wi[0];
+      for (int w = 1; w < nw; ++w)
+        if (s_wv[w] > v || (s_wv[w] == v && s_wi[w] < k)) { v = s_wv[w]; k = s_wi[w]; }
+      s_p = k;
+    }
+    __syncthreads();
+    const int p = s_p;
+    // exact norm of the pivot column over rows i..m-1
+    if (warp == 0) {
+      double s = 0.0;
+      for (int k = i + lane; k < m; k += 32) s += abs2(a[k + (int64_t)p * m]);
+      s = warp_sum(s);
+      if (lane == 0) s_nrm = sqrt(s);
+    }
+    __syncthreads();
+    const double nrm = s_nrm;
+    if (i == 0) R00 = nrm;
+    if (!(nrm > tol * R00) || nrm == 0.0) { r = i; break; }
+    // swap columns i and p
+    if (p != i) {
+      for (int k = tid; k < m; k += NT) {
+        double2 t = a[k + (int64_t)i * m];
+        a[k + (int64_t)i * m] = a[k + (int64_t)p * m];
+        a[k + (int64_t)p * m] = t;
+      }
+      if (tid == 0) {
+        double t = cn[i]; cn[i] = cn[p]; cn[p] = t;
+        t = cref[i]; cref[i] = cref[p]; cref[p] = t;
+        int q = pv[i]; pv[i] = pv[p]; pv[p] = q;
+      }
+    }
+    __syncthreads();
+    // Householder reflector for column i: H x = alpha e1, alpha = -exp(j arg x0) |x|
+    if (tid == 0) {
+      double2 x0 = a[i + (int64_t)i * m];
+      double ax0 = sqrt(abs2(x0));
+      double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+      double2 alpha = make_double2(-ph.x * nrm, -ph.y * nrm);
+      rd[i] = alpha;
+      double2 v0 = make_double2(x0.x - alpha.x, x0.y - alpha.y);
+      s_v0 = v0;
+      s_vn2 = 2.0 * nrm * nrm + 2.0 * nrm * ax0;  // v^H v
+      a[i + (int64_t)i * m] = v0;
+    }
+    __syncthreads();
+    const double inv = s_vn2 > 0.0 ? 2.0 / s_vn2 : 0.0;
+    const double2* v = a + (int64_t)i * m;
+    for (int j = i + 1 + warp; j < n; j += nw) {
+      double2* col = a + (int64_t)j * m;
+      double wr = 0.0, wi = 0.0;
+      for (int k = i + lane; k < m; k += 32) {
+        double2 t = cconjmul(v[k], col[k]);
+        wr += t.x; wi += t.y;
+      }
+      wr = warp_sum(wr);
+      wi = warp_sum(wi);
+      const double2 f = make_double2(wr * inv, wi * inv);
+      for (int k = i + lane; k < m; k += 32) {
+        double2 t = cmul(v[k], f);
+        col[k].x -= t.x;
+        col[k].y -= t.y;
+      }
+      __syncwarp();
+      // downdate the norm of the remaining rows i+1..m-1
+      double nn = cn[j] - abs2(col[i]);
+      if (nn <= 1e-4 * cref[j]) {
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < m; k += 32) s += abs2(col[k]);
+        nn = warp_sum(s);
+        if (lane == 0) cref[j] = nn;
+      }
+      if (lane == 0) cn[j] = fmax(nn, 0.0);
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  // T = R11^-1 R12, in place in rows 0..r-1 of columns r..n-1
+  for (int c = r + tid; c < n; c += NT) {
+    double2* col = a + (int64_t)c * m;
+    for (int k = r - 1; k >= 0; --k) {
+      double2 t = col[k];
+      for (int l = k + 1; l < r; ++l) {
+        double2 u = cmul(a[k + (int64_t)l * m], col[l]);
+        t.x -= u.x; t.y -= u.y;
+      }
+      double2 d = rd[k];
+      double dd = abs2(d);
+      col[k] = make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd);
+    }
+  }
+  __syncthreads();
+  double2* V = Vpool + J.v_off;
+  for (int64_t e = tid; e < (int64_t)r * n; e += NT) {
+    int k = int(e / n), c = int(e % n);
+    V[(int64_t)k * n + pv[c]] = c < r ? make_double2(c == k ? 1.0 : 0.0, 0.0) : a[k + (int64_t)c * m];
+  }
+  int32_t* po = pivpool + J.p_off;
+  for (int c = tid; c < n; c += NT) po[c] = pv[c];
+  if (tid == 0) rank_out[blockIdx.x] = r;
+}
+
+void id_batched(const IdJob* d_jobs, int njobs, int max_n, double2* d_a, double2* d_v, int32_t* d_piv,
+                int32_t* d_rank, double tol, cudaStream_t s) {
+  if (njobs <= 0) return;
+  constexpr int NT = 256;
+  size_t smem = sizeof(double) * 2 * max_n + sizeof(double2) * max_n + sizeof(int) * max_n + 64;
+  VIE_REQUIRE(smem <= 200 * 1024, VIE_ENOTSUP, "ID block too wide for shared memory");
+  VIE_CUDA(cudaFuncSetAttribute(id_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  id_kernel<NT><<<njobs, NT, smem, s>>>(d_jobs, d_a, d_v, d_piv, d_rank, tol);
+  VIE_CUDA(cudaGetLastError());
+}
+
+}  // namespace vie

@@ -1,0 +1,229 @@
+// Internal declarations shared by the translation units of libvie.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vie.h"
+
+namespace vie {
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+
+struct Error {
+  vie_status status;
+  std::string msg;
+};
+
+#define VIE_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      throw ::vie::Error{VIE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define VIE_REQUIRE(cond, status, msg)                   \
+  do {                                                   \
+    if (!(cond)) throw ::vie::Error{(status), (msg)};    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory owned by the operator
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t n);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// mesh (host): voxels -> Kuhn tets -> faces (SWG table), Sec. II / Eq. (3)
+// ---------------------------------------------------------------------------
+struct Mesh {
+  double h = 0;
+  int64_t nvox = 0, nt = 0, nf = 0, nv = 0;
+  std::vector<int32_t> vox;        // 3*nvox
+  std::vector<double> eps;         // 2*nvox
+  std::vector<int32_t> tets;       // 4*nt vertex ids
+  std::vector<int32_t> vlat;       // 3*nv lattice coordinates of the vertices
+  std::vector<int32_t> faces;      // 3*nf sorted vertex ids
+  std::vector<int32_t> tp, tm, lp, lm;  // nf: T+, T-, local face index in T+ / T-
+  std::vector<int32_t> tet_faces;  // 4*nt
+};
+void build_mesh(const vie_voxels& body, Mesh& m);
+
+// Kuhn tetrahedra: offsets of the 4 vertices of the 6 types from the voxel corner.
+extern const int kKuhn[6][4][3];
+
+// ---------------------------------------------------------------------------
+// cluster tree (host), Sec. III-A
+// ---------------------------------------------------------------------------
+struct Tree {
+  int levels = 0;                       // L_H
+  std::vector<int32_t> perm;            // tree position -> original face
+  std::vector<std::vector<int64_t>> bounds;  // bounds[l]: 2^l + 1 offsets
+  std::vector<std::vector<double>> bbox;     // bbox[l]: 6 doubles per node (lo xyz, hi xyz)
+};
+void build_tree(const std::vector<double>& pts /*3n*/, int leaf, Tree& t);
+
+// ---------------------------------------------------------------------------
+// quadrature rules (host), barycentric with weights summing to 1
+// ---------------------------------------------------------------------------
+struct Rule {
+  int n = 0;
+  std::vector<double> lam;  // n * (4 or 3)
+  std::vector<double> w;
+};
+Rule rule_tet4();
+Rule rule_tri3();
+Rule rule_tet_conical(int n);
+Rule rule_tri_conical(int n);
+
+// ---------------------------------------------------------------------------
+// device geometry + entry evaluator (entries.cu)
+// ---------------------------------------------------------------------------
+struct FaceDev {
+  int32_t tp, tm;      // owner tets (tm = -1 on the boundary)
+  int8_t lp, lm;       // local face indices
+  int8_t boundary;     // half-SWG: test surface density -1
+  int8_t pad;
+  double jump_re, jump_im;  // source surface density kappa(T-) - kappa(T+)
+};
+
+struct TetDev {
+  int32_t vx, vy, vz;  // voxel
+  int32_t type;        // Kuhn type 0..5
+  double kap_re, kap_im;      // kappa
+  double inveps_re, inveps_im;
+};
+
+struct Geometry {
+  int64_t n = 0, nt = 0;
+  double h = 0, k0 = 0;
+  DevBuf faces;   // FaceDev[n]
+  DevBuf tets;    // TetDev[nt]
+  DevBuf table;   // near / mid tier interaction table (FP64)
+};
+void geometry_upload(const Mesh& m, double k0, Geometry& g, cudaStream_t s);
+void geometry_table(Geometry& g, cudaStream_t s);   // computes the near/mid table
+
+// One dense block of Z to evaluate: out[i + j*ld] = Z(rows[i], cols[j]) (col-major, c128).
+struct EntryBlock {
+  int64_t out_off;   // element offset into the output pool
+  int64_t row_off;   // offset into the row index pool
+  int64_t col_off;   // offset into the col index pool
+  int32_t m, n;      // rows, cols
+};
+void entries_blocks(const Geometry& g, const EntryBlock* d_blocks, const int64_t* d_prefix,
+                    int nblocks, int64_t total, const int32_t* d_rows, const int32_t* d_cols,
+                    double2* d_out, cudaStream_t s);
+void entries_pairs(const Geometry& g, const int32_t* rows, const int32_t* cols, int64_t count,
+                   double2* out, cudaStream_t s);
+void rhs_planewave(const Geometry& g, const double* khat, const double* pol, int nrhs, double2* V,
+                   cudaStream_t s);
+void farfield(const Geometry& g, const double2* I, int nrhs, const double* dirs, int ndir,
+              double* rcs, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// batched interpolative decomposition (id.cu), Eq. (7)
+// ---------------------------------------------------------------------------
+struct IdJob {
+  int64_t a_off;   // col-major m x n input (destroyed), c128
+  int64_t v_off;   // row-major r x n output V = [I T] P^T, c128 (space min(m,n)*n)
+  int64_t p_off;   // n ints: pivot order (first r = skeleton)
+  int32_t m, n;
+};
+void id_batched(const IdJob* d_jobs, int njobs, int max_n, double2* d_a, double2* d_v, int32_t* d_piv,
+                int32_t* d_rank, double tol, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// apply program (apply.cu)
+// ---------------------------------------------------------------------------
+enum Space : int32_t { SP_X = 0, SP_Y = 1, SP_C = 2 };
+
+struct OpDesc {          // y[out] (=|+=) A (M x K, row-major, ld) * x[in]
+  int64_t mat_off;       // element offset of A in the stage's matrix buffer
+  int64_t in_off, out_off;
+  int32_t M, K, ld;
+  int16_t in_space, out_space;
+  int32_t accumulate;    // 0: assign, 1: add
+  int32_t pad;
+};
+
+struct Tile {            // a warp's unit of work: rows [r0, r0 + nr) of op `op`
+  int32_t op, r0, nr, g; // g = lanes per row (power of two)
+};
+
+struct Stage {
+  DevBuf mats;           // packed factor matrices (c64 or c128)
+  DevBuf ops;            // OpDesc[nops]
+  DevBuf tiles;          // Tile[ntiles]
+  int64_t nops = 0, ntiles = 0, entries = 0, bytes = 0;
+};
+
+struct Program {         // one operator's apply: gather, stages, scatter
+  std::vector<Stage> stages;
+  int64_t n = 0, ncoef = 0;
+  int factor_dtype = VIE_C64;
+  int64_t entries = 0, bytes = 0;
+};
+
+void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles);
+void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs,
+                   int64_t ldx, int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c,
+                   cudaStream_t s, cudaEvent_t* events = nullptr);
+int64_t program_launches(const Program& p, int64_t nrhs);
+void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* d_src_ld,
+                   const int32_t* d_src_colmajor, const int64_t* d_dst_off, const int32_t* d_M,
+                   const int32_t* d_K, const int32_t* d_ld, int nmat, void* dst, int dst_dtype,
+                   cudaStream_t s);
+
+struct BuildResult {
+  int64_t entries_evaluated = 0;
+  int max_rank = 0;
+};
+
+}  // namespace vie
+
+struct vie_op;
+namespace vie {
+void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res);
+void ensure_ws(vie_op* h, const Program& p, int64_t nrhs, int dtype);
+void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dtype, cudaStream_t s);
+void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int restart, int max_iter,
+                 int32_t* iters_out, double* relres_out, cudaStream_t s, bool& converged_all);
+void farfield_impl(const Geometry& g, const int32_t* d_tet_faces, const double2* I, int nrhs, const double* dirs,
+                   int ndir, double* rcs, cudaStream_t s);
+}  // namespace vie
+
+// The operator handle
+struct vie_op {
+  vie::Mesh mesh;
+  vie::Tree tree;
+  vie::Geometry geo;
+  vie::DevBuf perm;      // int32 tree -> original
+  vie::DevBuf tet_faces; // int32 4*nt
+  vie::Program z, zinv;
+  bool has_zinv = false;
+  vie::DevBuf xt, yt, coef;  // apply workspaces (grown on demand)
+  size_t ws_bytes = 0;
+  vie_config cfg{};
+  vie_stats_t stats{};
+};
