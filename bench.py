@@ -11,7 +11,7 @@ algorithmic bytes are 8 E + 16 N nrhs (E = complex entries of all stored
 factor blocks, c64; X read once, Y written once).  The factor data (tens of
 GB) is far larger than L2, so no flush is needed between steps.
 
-Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--small]
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--radius R]
 Under torchrun each rank builds its own replica (weak scaling, no collective on
 the data path) and rank 0 prints one JSON line.
 """
@@ -47,10 +47,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload(small: bool):
-    if small:
-        return W.sphere(0.6, 4.0 - 0.1j, 1.0 / 10, name="sphere_r0.6_eps4-0.1j"), "sphere r=0.6 (small check)"
-    return W.sphere_large_c32(), "sphere r=2 lambda0, eps_r=4-0.1j, pitch lambda0/10, N=410208"
+def workload(radius: float):
+    """Homogeneous sphere of the given radius, eps_r = 4 - 0.1j, pitch lambda0/10 (radius 2: N = 410,208)."""
+    body = W.sphere(radius, 4.0 - 0.1j, 1.0 / 10, name=f"sphere_r{radius:g}_eps4-0.1j")
+    desc = f"sphere r={radius:g} lambda0, eps_r=4-0.1j, pitch lambda0/10, 6 Kuhn tets/voxel, N={{n}}"
+    return body, desc
 
 
 class ClockSampler:
@@ -106,8 +107,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_apply_sample(seconds_budget: float = 20.0):
-    """Time the FP64 oracle's HOD-BF apply on a bounded sample of the workload (host cores)."""
+def oracle_operator():
+    """The FP64 oracle's HOD-BF of a bounded sample of the workload: a sphere of the same
+    permittivity at radius 0.25 and pitch 1/16 (N = 3,672), built with full-row IDs."""
     from oracle.entries import Elements, zblock
     from oracle.hodbf import HODBF, cluster_tree, face_centroids
     from oracle.mesh import build_mesh
@@ -119,6 +121,17 @@ def oracle_apply_sample(seconds_budget: float = 20.0):
     perm, LH, bounds = cluster_tree(face_centroids(mesh), 64)
     Zt = Z[np.ix_(perm, perm)]
     H = HODBF(lambda r, c: Zt[np.ix_(r, c)], bounds, LH, 1e-4)
+    return H, n
+
+
+def oracle_sample_desc(H, n, reps, dt):
+    return (f"oracle FP64 HOD-BF apply of a sphere r=0.25 eps_r=4-0.1j pitch 1/16 (N={n}, chi_con=1e-4, "
+            f"{H.entries()} complex128 entries), {reps} applies of {dt * 1e3:.2f} ms")
+
+
+def oracle_apply_sample(seconds_budget: float = 15.0):
+    """Time the FP64 oracle's HOD-BF apply on host cores (bounded sample of the workload)."""
+    H, n = oracle_operator()
     x = W.random_block(n, 1, seed=1)
     nbytes = 16 * H.entries() + 32 * n  # complex128 factors, x read and y written
     reps, t0 = 0, time.perf_counter()
@@ -128,31 +141,36 @@ def oracle_apply_sample(seconds_budget: float = 20.0):
     dt = (time.perf_counter() - t0) / reps
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return dict(value=nbytes / dt / 1e9, unit=UNIT, cores=cores, kind="oracle",
-                sample=f"oracle FP64 HOD-BF apply of a sphere r=0.25 eps_r=4-0.1j pitch 1/16 (N={n}, "
-                       f"chi_con=1e-4, {H.entries()} entries), {reps} applies, {dt * 1e3:.1f} ms each",
-                ms_per_apply=dt * 1e3, n=n)
+                sample=oracle_sample_desc(H, n, reps, dt), ms_per_apply=dt * 1e3, n=n)
 
 
 def run_reference(args):
+    """The oracle arm: the plain FP64 CPU HOD-BF apply, timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    base = oracle_apply_sample(5.0)
-    vals = []
+    H, n = oracle_operator()
+    x = W.random_block(n, 1, seed=1)
+    nbytes = 16 * H.entries() + 32 * n
     for _ in range(args.warmup):
-        pass
+        H.apply(x)
+    times = []
     for _ in range(args.steps):
-        s = oracle_apply_sample(2.0)
-        vals.append(s["value"])
-    v = statistics.median(vals) if vals else base["value"]
-    _, desc = workload(args.small)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_apply"],
+        t0 = time.perf_counter()
+        H.apply(x)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
+    v = nbytes / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    _, desc = workload(args.radius)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": desc + " (oracle on a bounded sample)"},
-            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    line["cpu_baseline"]["value"] = v
+            "data": "synthetic",
+            "config": {"workload": desc.format(n="410208") + " (oracle on a bounded sample, see cpu_baseline)"},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": oracle_sample_desc(H, n, args.steps, dt)},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -160,10 +178,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--small", action="store_true", help="small workload (quick functional check)")
+    ap.add_argument("--radius", type=float, default=2.0,
+                    help="sphere radius in wavelengths (2.0 = the benchmark workload; smaller for checks/profiles)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -183,7 +202,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     hbm, peak_kind = peaks()
-    body, desc = workload(args.small)
+    body, desc = workload(args.radius)
     t0 = time.perf_counter()
     op = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c64", seed=1)
     build_s = time.perf_counter() - t0
@@ -253,7 +272,7 @@ def main():
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": desc, "n": n, "levels": st.levels, "chi_con": 1e-4, "leaf": 64, "nrhs": 1,
+            "config": {"workload": desc.format(n=n), "n": n, "levels": st.levels, "chi_con": 1e-4, "leaf": 64, "nrhs": 1,
                        "factor_entries": E, "factor_bytes_stored": int(sbytes.sum()), "max_rank": st.max_rank,
                        "build_seconds": round(build_s, 2), "l2": "inputs (factor data) larger than L2, no flush",
                        "parallelism": f"replicas x{world}"},

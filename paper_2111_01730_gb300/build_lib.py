@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3,-ffp-contract=off", "--expt-relaxed-constexpr"]
-SOURCES = ["host.cpp", "api.cpp", "entries.cu", "id.cu", "build.cu", "apply.cu", "solve.cu", "tc.cu"]
+SOURCES = ["host.cpp", "api.cpp", "entries.cu", "id.cu", "build.cu", "apply.cu", "solve.cu", "inverse.cu", "tc.cu"]
 
 
 def _compile(src: str) -> str:
@@ -30,7 +30,7 @@ def build(verbose: bool = False) -> str:
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(_compile, srcs))
-    cmd = [NVCC, *ARCH, "-shared", "-o", OUT, *objs, "-Xcompiler", "-fopenmp", "-lgomp"]
+    cmd = [NVCC, *ARCH, "-shared", "-o", OUT, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lcublas", "-lcusolver"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

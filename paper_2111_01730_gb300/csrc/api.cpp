@@ -115,6 +115,17 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, v
       h->stats.entries_evaluated = br.entries_evaluated;
       h->stats.apply_stages_z = (int32_t)h->z.stages.size();
       h->stats.build_seconds = now_s() - t0;
+      if (cfg->tol_fact > 0) {
+        double t1 = now_s();
+        BuildResult bi;
+        build_inverse(h, s, bi);
+        VIE_CUDA(cudaStreamSynchronize(s));
+        h->stats.entries_zinv = h->zinv.entries;
+        h->stats.bytes_zinv = h->zinv.bytes;
+        h->stats.apply_stages_zinv = (int32_t)h->zinv.stages.size();
+        h->stats.max_rank = std::max(h->stats.max_rank, bi.max_rank);
+        h->stats.invert_seconds = now_s() - t1;
+      }
     } catch (...) {
       delete h;
       throw;

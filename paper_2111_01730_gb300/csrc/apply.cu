@@ -37,15 +37,31 @@ template <>
 __device__ __forceinline__ void row_dot<float, float, 1>(const float2* __restrict__ A, int K, int li, int g,
                                                           const float2* __restrict__ x, int nrhs,
                                                           float (&re)[1], float (&im)[1]) {
+  // four independent 16-byte loads in flight per lane (memory-level parallelism)
   const float4* A4 = reinterpret_cast<const float4*>(A);
-  for (int k = 2 * li; k < K; k += 2 * g) {
-    float4 a = __ldcs(A4 + (k >> 1));
-    float2 x0 = __ldg(x + k);
-    float2 x1 = (k + 1 < K) ? __ldg(x + k + 1) : make_float2(0.f, 0.f);
-    re[0] = fmaf(a.x, x0.x, re[0]); re[0] = fmaf(-a.y, x0.y, re[0]);
-    im[0] = fmaf(a.x, x0.y, im[0]); im[0] = fmaf(a.y, x0.x, im[0]);
-    re[0] = fmaf(a.z, x1.x, re[0]); re[0] = fmaf(-a.w, x1.y, re[0]);
-    im[0] = fmaf(a.z, x1.y, im[0]); im[0] = fmaf(a.w, x1.x, im[0]);
+  constexpr int U = 4;
+  for (int k0 = 2 * li; k0 < K; k0 += 2 * g * U) {
+    float4 a[U];
+    float2 x0[U], x1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + 2 * g * u;
+      if (k < K) {
+        a[u] = __ldcs(A4 + (k >> 1));
+        x0[u] = __ldg(x + k);
+        x1[u] = (k + 1 < K) ? __ldg(x + k + 1) : make_float2(0.f, 0.f);
+      } else {
+        a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        x0[u] = x1[u] = make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      re[0] = fmaf(a[u].x, x0[u].x, re[0]); re[0] = fmaf(-a[u].y, x0[u].y, re[0]);
+      im[0] = fmaf(a[u].x, x0[u].y, im[0]); im[0] = fmaf(a[u].y, x0[u].x, im[0]);
+      re[0] = fmaf(a[u].z, x1[u].x, re[0]); re[0] = fmaf(-a[u].w, x1[u].y, re[0]);
+      im[0] = fmaf(a[u].z, x1[u].y, im[0]); im[0] = fmaf(a[u].w, x1[u].x, im[0]);
+    }
   }
 }
 
@@ -102,7 +118,7 @@ __global__ void __launch_bounds__(256) stage_kernel(const OpDesc* __restrict__ o
     const OpDesc op = ops[tl.op];
     const int g = tl.g, rp = 32 / g;
     const int li = lane & (g - 1);
-    const V2* xin = (op.in_space == SP_X ? xt : coef) + op.in_off * nrhs + rhs0;
+    const V2* xin = (op.in_space == SP_X ? xt : (op.in_space == SP_Y ? (const V2*)yt : coef)) + op.in_off * nrhs + rhs0;
     V2* yout = (op.out_space == SP_Y ? yt : coef) + op.out_off * nrhs + rhs0;
     for (int r = tl.r0 + lane / g; r < tl.r0 + tl.nr; r += rp) {
       const bool active = r < op.M;

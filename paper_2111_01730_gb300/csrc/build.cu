@@ -122,9 +122,11 @@ struct Sampler {
 };
 
 struct BF {
-  int l;
-  int64_t i;
+  int l;          // tree level of the row node o (and of the column node s)
+  int64_t i;      // index of o at level l
+  int64_t si;     // index of s at level l (the sibling for Z, o itself for E_tau)
   int L;
+  int src;        // entry source index (dense E_tau matrices)
   std::vector<std::vector<int32_t>> rank;            // rank[k][blk]
   std::vector<std::vector<int64_t>> coff;            // coefficient offsets
   std::vector<std::vector<std::vector<int32_t>>> skel;  // skeleton tree positions (last level only kept)
@@ -170,7 +172,42 @@ static void finalize_stage(Stage& st, const std::vector<OpDesc>& ops, std::vecto
   chunks.clear();
 }
 
+// Z entries from the FP64 evaluator (tree positions mapped to faces)
+void ZEntrySource::eval(const std::vector<EntryBlock>& eb, const std::vector<int64_t>& prefix,
+                        const std::vector<int32_t>& rows, const std::vector<int32_t>& cols,
+                        const std::vector<int32_t>& /*srcs*/, int64_t total, double2* dA, cudaStream_t s) {
+  const auto& perm = h->tree.perm;
+  std::vector<int32_t> r(rows.size()), c(cols.size());
+  for (size_t i = 0; i < rows.size(); ++i) r[i] = perm[rows[i]];
+  for (size_t i = 0; i < cols.size(); ++i) c[i] = perm[cols[i]];
+  const int nj = (int)eb.size();
+  DevBuf drows, dcols, deb, dpre;
+  drows.alloc(sizeof(int32_t) * std::max<size_t>(1, r.size()));
+  dcols.alloc(sizeof(int32_t) * std::max<size_t>(1, c.size()));
+  deb.alloc(sizeof(EntryBlock) * nj);
+  dpre.alloc(sizeof(int64_t) * nj);
+  VIE_CUDA(cudaMemcpyAsync(drows.p, r.data(), sizeof(int32_t) * r.size(), cudaMemcpyHostToDevice, s));
+  VIE_CUDA(cudaMemcpyAsync(dcols.p, c.data(), sizeof(int32_t) * c.size(), cudaMemcpyHostToDevice, s));
+  VIE_CUDA(cudaMemcpyAsync(deb.p, eb.data(), sizeof(EntryBlock) * nj, cudaMemcpyHostToDevice, s));
+  VIE_CUDA(cudaMemcpyAsync(dpre.p, prefix.data(), sizeof(int64_t) * nj, cudaMemcpyHostToDevice, s));
+  entries_blocks(h->geo, deb.as<EntryBlock>(), dpre.as<int64_t>(), nj, total, drows.as<int32_t>(), dcols.as<int32_t>(),
+                 dA, s);
+  VIE_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
+  // Z: every sibling pair (tau, tau^1) at every level l >= 1, plus dense leaf blocks
+  std::vector<BfSpec> specs;
+  for (int l = 1; l <= h->tree.levels; ++l)
+    for (int64_t i = 0; i < (int64_t(1) << l); ++i) specs.push_back(BfSpec{l, i, i ^ 1, 0});
+  ZEntrySource src(h);
+  h->z.stages.clear();
+  h->z.ncoef = 0;
+  build_program(h, specs, src, h->cfg.tol_con, h->z, /*leaf_blocks=*/true, SP_X, s, res);
+}
+
+void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src, double tol, Program& P,
+                   bool leaf_blocks, int v0_space, cudaStream_t s, BuildResult& res) {
   const Tree& t = h->tree;
   const int LH = t.levels;
   const int64_t N = h->mesh.nf;
@@ -188,27 +225,29 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
   Sampler smp{t, pts, LH, cfg.seed, cfg.oversample};
   // butterflies
   std::vector<BF> bfs;
-  for (int l = 1; l <= LH; ++l)
-    for (int64_t i = 0; i < (int64_t(1) << l); ++i) {
-      BF b;
-      b.l = l; b.i = i; b.L = LH - l;
-      b.rank.resize(b.L + 1);
-      b.coff.resize(b.L + 1);
-      bfs.push_back(std::move(b));
-    }
-  Program& P = h->z;
+  int Lmax = -1;
+  for (const BfSpec& sp : specs) {
+    BF b;
+    b.l = sp.level; b.i = sp.o; b.si = sp.s; b.L = LH - sp.level; b.src = sp.src;
+    b.rank.resize(b.L + 1);
+    b.coff.resize(b.L + 1);
+    Lmax = std::max(Lmax, b.L);
+    bfs.push_back(std::move(b));
+  }
   P.n = N;
   P.factor_dtype = cfg.factor_dtype;
-  const int nstages = LH + 1;  // stage k: V^0/D (k = 0), W^k and B of L = k - 1
-  P.stages.clear();
-  P.stages.resize(nstages);
-  int64_t coef_next = 0;
+  // stage k: V^0 (+ leaf blocks) for k = 0, W^k and the B^L of L = k - 1 for k >= 1
+  const int nstages = std::max(Lmax + 2, leaf_blocks ? 1 : 0);
+  const int stage_base = (int)P.stages.size();
+  P.stages.resize(stage_base + nstages);
+  int64_t coef_next = P.ncoef;
   const size_t budget = size_t(8) << 30;  // bytes of c128 scratch per chunk
+  const double tol_id = tol;
 
   for (int k = 0; k < nstages; ++k) {
     // ---- collect the jobs of this batch ----
     std::vector<Job> jobs;
-    if (k == 0)
+    if (k == 0 && leaf_blocks)
       for (int64_t i = 0; i < (int64_t(1) << LH); ++i) {
         Job j{-1, 0, i, false, {}, {}};
         for (int64_t p = t.bounds[LH][i]; p < t.bounds[LH][i + 1]; ++p) { j.rows.push_back((int32_t)p); }
@@ -218,7 +257,7 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
     for (int b = 0; b < (int)bfs.size(); ++b) {
       BF& B = bfs[b];
       const int lo = B.l, L = B.L;
-      const int64_t so = B.i ^ 1;
+      const int64_t so = B.si;
       if (k <= L) {
         const int64_t ntau = int64_t(1) << k, nnu = int64_t(1) << (L - k);
         for (int64_t ti = 0; ti < ntau; ++ti)
@@ -259,7 +298,7 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
       const int tlev = B.l + j.k;
       const int64_t tidx = B.i * (int64_t(1) << j.k) + ti;
       const int nlev = B.l + B.L - j.k;
-      const int64_t nidx = (B.i ^ 1) * nnu + nj;
+      const int64_t nidx = B.si * nnu + nj;
       uint64_t key = ((uint64_t)j.bf << 40) ^ ((uint64_t)j.k << 32) ^ (uint64_t)j.blk;
       smp.rows(tlev, tidx, nlev, nidx, (int)j.cols.size(), key, j.rows);
     }
@@ -293,23 +332,17 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
         Job& j = jobs[q0 + q];
         eb[q] = EntryBlock{aoff, (int64_t)rows.size(), (int64_t)cols.size(), (int32_t)j.rows.size(), (int32_t)j.cols.size()};
         prefix[q] = aoff;
-        for (int32_t p : j.rows) rows.push_back(t.perm[p]);
-        for (int32_t p : j.cols) cols.push_back(t.perm[p]);
+        for (int32_t p : j.rows) rows.push_back(p);  // tree positions; the source maps them
+        for (int32_t p : j.cols) cols.push_back(p);
         aoff += (int64_t)j.rows.size() * j.cols.size();
       }
       res.entries_evaluated += aoff;
-      DevBuf drows, dcols, deb, dpre, dA;
-      drows.alloc(sizeof(int32_t) * std::max<size_t>(1, rows.size()));
-      dcols.alloc(sizeof(int32_t) * std::max<size_t>(1, cols.size()));
-      deb.alloc(sizeof(EntryBlock) * nj);
-      dpre.alloc(sizeof(int64_t) * nj);
+      DevBuf dA;
       dA.alloc(sizeof(double2) * std::max<int64_t>(1, aoff));
-      VIE_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
-      VIE_CUDA(cudaMemcpyAsync(dcols.p, cols.data(), sizeof(int32_t) * cols.size(), cudaMemcpyHostToDevice, s));
-      VIE_CUDA(cudaMemcpyAsync(deb.p, eb.data(), sizeof(EntryBlock) * nj, cudaMemcpyHostToDevice, s));
-      VIE_CUDA(cudaMemcpyAsync(dpre.p, prefix.data(), sizeof(int64_t) * nj, cudaMemcpyHostToDevice, s));
-      entries_blocks(h->geo, deb.as<EntryBlock>(), dpre.as<int64_t>(), nj, aoff, drows.as<int32_t>(),
-                     dcols.as<int32_t>(), dA.as<double2>(), s);
+      std::vector<int32_t> srcs(nj);
+      for (int q = 0; q < nj; ++q)  // leaf blocks carry their leaf index as the source
+        srcs[q] = jobs[q0 + q].bf >= 0 ? bfs[jobs[q0 + q].bf].src : (int32_t)jobs[q0 + q].blk;
+      src.eval(eb, prefix, rows, cols, srcs, aoff, dA.as<double2>(), s);
       // IDs
       std::vector<IdJob> ij;
       std::vector<int> ij_q;
@@ -334,7 +367,7 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
         drank.alloc(sizeof(int32_t) * ij.size());
         VIE_CUDA(cudaMemcpyAsync(dij.p, ij.data(), sizeof(IdJob) * ij.size(), cudaMemcpyHostToDevice, s));
         id_batched(dij.as<IdJob>(), (int)ij.size(), maxn, dA.as<double2>(), dV.as<double2>(), dpiv.as<int32_t>(),
-                   drank.as<int32_t>(), cfg.tol_con, s);
+                   drank.as<int32_t>(), tol_id, s);
         VIE_CUDA(cudaMemcpyAsync(piv.data(), dpiv.p, sizeof(int32_t) * poff, cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaMemcpyAsync(rk.data(), drank.p, sizeof(int32_t) * ij.size(), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaStreamSynchronize(s));
@@ -361,6 +394,7 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
           OpDesc o{};
           o.mat_off = stage_off + mo; o.M = m; o.K = m; o.ld = (m + 1) & ~1;
           o.in_space = SP_X; o.in_off = j.rows[0]; o.out_space = SP_Y; o.out_off = j.rows[0]; o.accumulate = 0;
+          res.leaf_entries += (int64_t)m * m;
           ops.push_back(o);
           continue;
         }
@@ -394,7 +428,7 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
         o.accumulate = 0;
         const int64_t nnu = int64_t(1) << (B.L - j.k);
         if (j.k == 0) {
-          o.in_space = SP_X;
+          o.in_space = (int16_t)v0_space;
           o.in_off = j.cols[0];  // the leaf nu is a contiguous range of tree positions
         } else {
           o.in_space = SP_C;
@@ -466,7 +500,7 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
         o.out_off = bfs[o.pad].coff[k][blk];
         o.pad = 0;
       }
-    finalize_stage(P.stages[k], ops, chunks, chunk_elems, elem_bytes, s);
+    finalize_stage(P.stages[stage_base + k], ops, chunks, chunk_elems, elem_bytes, s);
   }
   P.ncoef = coef_next;
   P.entries = 0;

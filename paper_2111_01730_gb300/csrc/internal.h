@@ -197,14 +197,40 @@ void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* 
 
 struct BuildResult {
   int64_t entries_evaluated = 0;
+  int64_t leaf_entries = 0;
   int max_rank = 0;
+};
+
+// Where the builder takes matrix entries from (tree positions in, c128 col-major blocks out).
+struct EntrySource {
+  virtual ~EntrySource() = default;
+  virtual void eval(const std::vector<EntryBlock>& eb, const std::vector<int64_t>& prefix,
+                    const std::vector<int32_t>& rows, const std::vector<int32_t>& cols,
+                    const std::vector<int32_t>& srcs, int64_t total, double2* dA, cudaStream_t s) = 0;
+};
+
+// One butterfly to build: row node o and column node s at tree level `level`.
+struct BfSpec {
+  int level;
+  int64_t o, s;
+  int src;
 };
 
 }  // namespace vie
 
 struct vie_op;
 namespace vie {
+struct ZEntrySource : EntrySource {
+  vie_op* h;
+  explicit ZEntrySource(vie_op* hh) : h(hh) {}
+  void eval(const std::vector<EntryBlock>& eb, const std::vector<int64_t>& prefix, const std::vector<int32_t>& rows,
+            const std::vector<int32_t>& cols, const std::vector<int32_t>& srcs, int64_t total, double2* dA,
+            cudaStream_t s) override;
+};
 void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res);
+void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src, double tol, Program& P,
+                   bool leaf_blocks, int v0_space, cudaStream_t s, BuildResult& res);
+void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res);
 void ensure_ws(vie_op* h, const Program& p, int64_t nrhs, int dtype);
 void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dtype, cudaStream_t s);
 void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int restart, int max_iter,

@@ -1,0 +1,234 @@
+// HOD-BF approximate inverse Zinv (Sec. III-B, Algorithm 1), built on the GPU.
+//
+// Algorithm 1 writes the inverse of every diagonal block recursively as
+//   D_tau^-1 = (I + E_tau) diag(D_tau1^-1, D_tau2^-1),
+//   E_tau    = [I, B'_tau1; B'_tau2, I]^-1 - I,   B'_taui = D_taui^-1 B_taui,
+// and compresses each E_tau (a tau x tau block) as a butterfly at chi_fact.
+// Applying Zinv is then: y = D_leaf^-1 x on the leaves, followed, level by
+// level from the leaves to the root, by y_tau <- y_tau + E_tau y_tau.
+//
+// Construction here: for each node tau, E_tau is formed densely in complex
+// FP32 from its plain definition, E_tau = D_tau^-1 diag(D_tau1, D_tau2) - I
+// (the same matrix as above), with D_tau = Z(tau, tau) from the FP64 entry
+// evaluator, an LU factorization for D_tau^-1 and two GEMMs; it is then
+// compressed by the same ID-based butterfly construction as Z (Eqs. 7-10),
+// reading its entries from the dense matrix.  This replaces the randomized
+// recompression (BF_random_matvec inside BF_SMW, Algorithm 2) and is limited
+// by the dense top-level block (N^2 complex FP32 entries held three times).
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <chrono>
+
+#include "internal.h"
+
+namespace vie {
+
+#define VIE_CUBLAS(call)                                                                      \
+  do {                                                                                        \
+    cublasStatus_t st_ = (call);                                                              \
+    if (st_ != CUBLAS_STATUS_SUCCESS) throw Error{VIE_ECUDA, std::string(#call) + " failed"}; \
+  } while (0)
+#define VIE_CUSOLVER(call)                                                                      \
+  do {                                                                                          \
+    cusolverStatus_t st_ = (call);                                                              \
+    if (st_ != CUSOLVER_STATUS_SUCCESS) throw Error{VIE_ECUDA, std::string(#call) + " failed"}; \
+  } while (0)
+
+namespace {
+
+__global__ void c128_to_c64(const double2* a, float2* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+__global__ void set_identity(float2* a, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x)
+    a[e] = make_float2((e % n) == (e / n) ? 1.f : 0.f, 0.f);
+}
+
+__global__ void sub_identity(float2* a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i + i * n].x -= 1.f;
+}
+
+struct DenseRef {
+  const float2* p;
+  int64_t base;  // tree position of row/column 0
+  int64_t ld;
+};
+
+// out[block] (c128 col-major) = M_src[rows - base, cols - base]
+__global__ void gather_dense(const DenseRef* mats, const EntryBlock* blocks, const int64_t* prefix, const int32_t* src,
+                             int nblocks, int64_t total, const int32_t* rows, const int32_t* cols, double2* out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nblocks - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const EntryBlock b = blocks[lo];
+    const DenseRef M = mats[src[lo]];
+    int64_t k = g - prefix[lo];
+    int i = int(k % b.m), j = int(k / b.m);
+    float2 v = M.p[(rows[b.row_off + i] - M.base) + (cols[b.col_off + j] - M.base) * M.ld];
+    out[b.out_off + k] = make_double2(v.x, v.y);
+  }
+}
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+struct DenseSource : EntrySource {
+  std::vector<DenseRef> refs;
+  void eval(const std::vector<EntryBlock>& eb, const std::vector<int64_t>& prefix, const std::vector<int32_t>& rows,
+            const std::vector<int32_t>& cols, const std::vector<int32_t>& srcs, int64_t total, double2* dA,
+            cudaStream_t s) override {
+    const int nj = (int)eb.size();
+    DevBuf dref, deb, dpre, dsrc, drows, dcols;
+    dref.alloc(sizeof(DenseRef) * refs.size());
+    deb.alloc(sizeof(EntryBlock) * nj);
+    dpre.alloc(sizeof(int64_t) * nj);
+    dsrc.alloc(sizeof(int32_t) * nj);
+    drows.alloc(sizeof(int32_t) * std::max<size_t>(1, rows.size()));
+    dcols.alloc(sizeof(int32_t) * std::max<size_t>(1, cols.size()));
+    VIE_CUDA(cudaMemcpyAsync(dref.p, refs.data(), sizeof(DenseRef) * refs.size(), cudaMemcpyHostToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(deb.p, eb.data(), sizeof(EntryBlock) * nj, cudaMemcpyHostToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(dpre.p, prefix.data(), sizeof(int64_t) * nj, cudaMemcpyHostToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(dsrc.p, srcs.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(dcols.p, cols.data(), sizeof(int32_t) * cols.size(), cudaMemcpyHostToDevice, s));
+    if (total > 0)
+      gather_dense<<<grid_for(total), 256, 0, s>>>(dref.as<DenseRef>(), deb.as<EntryBlock>(), dpre.as<int64_t>(),
+                                                   dsrc.as<int32_t>(), nj, total, drows.as<int32_t>(),
+                                                   dcols.as<int32_t>(), dA);
+    VIE_CUDA(cudaGetLastError());
+    VIE_CUDA(cudaStreamSynchronize(s));
+  }
+};
+
+// D = Z(tau, tau) in complex FP32, column-major n x n (tree order within tau)
+void dense_block(vie_op* h, int64_t a, int64_t n, float2* D, cudaStream_t s) {
+  const auto& perm = h->tree.perm;
+  DevBuf rows, cols, tmp;
+  std::vector<int32_t> r(n);
+  for (int64_t i = 0; i < n; ++i) r[i] = perm[a + i];
+  rows.alloc(sizeof(int32_t) * n);
+  VIE_CUDA(cudaMemcpyAsync(rows.p, r.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+  const int64_t panel = std::max<int64_t>(1, (int64_t(1) << 26) / n);  // columns per panel
+  tmp.alloc(sizeof(double2) * n * std::min(panel, n));
+  cols.alloc(sizeof(int32_t) * n * std::min(panel, n));
+  DevBuf prow;
+  prow.alloc(sizeof(int32_t) * n * std::min(panel, n));
+  for (int64_t c0 = 0; c0 < n; c0 += panel) {
+    const int64_t nc = std::min(panel, n - c0);
+    std::vector<int32_t> pr(n * nc), pc(n * nc);
+    for (int64_t j = 0; j < nc; ++j)
+      for (int64_t i = 0; i < n; ++i) { pr[j * n + i] = r[i]; pc[j * n + i] = r[c0 + j]; }
+    VIE_CUDA(cudaMemcpyAsync(prow.p, pr.data(), sizeof(int32_t) * n * nc, cudaMemcpyHostToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(cols.p, pc.data(), sizeof(int32_t) * n * nc, cudaMemcpyHostToDevice, s));
+    entries_pairs(h->geo, prow.as<int32_t>(), cols.as<int32_t>(), n * nc, tmp.as<double2>(), s);
+    c128_to_c64<<<grid_for(n * nc), 256, 0, s>>>(tmp.as<double2>(), D + c0 * n, n * nc);
+    VIE_CUDA(cudaGetLastError());
+    VIE_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+// Dinv = D^-1 (D is overwritten by its LU factors)
+void dense_inverse(cusolverDnHandle_t sol, float2* D, float2* Dinv, int64_t n, cudaStream_t s) {
+  int lwork = 0;
+  VIE_CUSOLVER(cusolverDnCgetrf_bufferSize(sol, (int)n, (int)n, (cuComplex*)D, (int)n, &lwork));
+  DevBuf work, ipiv, info;
+  work.alloc(sizeof(cuComplex) * std::max(lwork, 1));
+  ipiv.alloc(sizeof(int) * n);
+  info.alloc(sizeof(int));
+  VIE_CUSOLVER(cusolverDnCgetrf(sol, (int)n, (int)n, (cuComplex*)D, (int)n, work.as<cuComplex>(), ipiv.as<int>(),
+                                info.as<int>()));
+  set_identity<<<grid_for(n * n), 256, 0, s>>>(Dinv, n);
+  VIE_CUSOLVER(cusolverDnCgetrs(sol, CUBLAS_OP_N, (int)n, (int)n, (const cuComplex*)D, (int)n, ipiv.as<int>(),
+                                (cuComplex*)Dinv, (int)n, info.as<int>()));
+  int hinfo = 0;
+  VIE_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA(cudaStreamSynchronize(s));
+  VIE_REQUIRE(hinfo == 0, VIE_ENAN, "singular diagonal block in the inverse construction");
+}
+
+}  // namespace
+
+void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
+  const Tree& t = h->tree;
+  const int LH = t.levels;
+  const int64_t N = h->mesh.nf;
+  VIE_REQUIRE((double)N * (double)N * 8.0 * 3.0 < 200e9, VIE_ENOTSUP,
+              "dense inverse construction limited to about 90k unknowns");
+  cusolverDnHandle_t sol = nullptr;
+  cublasHandle_t blas = nullptr;
+  VIE_CUSOLVER(cusolverDnCreate(&sol));
+  VIE_CUBLAS(cublasCreate(&blas));
+  struct Handles {
+    cusolverDnHandle_t s;
+    cublasHandle_t b;
+    ~Handles() { if (s) cusolverDnDestroy(s); if (b) cublasDestroy(b); }
+  } hd{sol, blas};
+  VIE_CUSOLVER(cusolverDnSetStream(sol, s));
+  VIE_CUBLAS(cublasSetStream(blas, s));
+  Program& P = h->zinv;
+  P.stages.clear();
+  P.ncoef = 0;
+  // leaves: dense inverses (stage 0: y = D_leaf^-1 x)
+  {
+    const auto& b = t.bounds[LH];
+    const int64_t nl = (int64_t)b.size() - 1;
+    std::vector<DevBuf> inv(nl);
+    DenseSource src;
+    for (int64_t i = 0; i < nl; ++i) {
+      const int64_t a = b[i], n = b[i + 1] - b[i];
+      DevBuf D;
+      D.alloc(sizeof(float2) * n * n);
+      inv[i].alloc(sizeof(float2) * n * n);
+      dense_block(h, a, n, D.as<float2>(), s);
+      dense_inverse(sol, D.as<float2>(), inv[i].as<float2>(), n, s);
+      src.refs.push_back(DenseRef{inv[i].as<float2>(), a, n});
+    }
+    build_program(h, {}, src, h->cfg.tol_fact, P, /*leaf_blocks=*/true, SP_X, s, res);
+  }
+  // levels L_H - 1 .. 0: E_tau = D_tau^-1 diag(D_tau1, D_tau2) - I, compressed at chi_fact
+  for (int l = LH - 1; l >= 0; --l) {
+    const auto& b = t.bounds[l];
+    const auto& bc = t.bounds[l + 1];
+    const int64_t nn = (int64_t)b.size() - 1;
+    std::vector<DevBuf> E(nn);
+    DenseSource src;
+    std::vector<BfSpec> specs;
+    for (int64_t i = 0; i < nn; ++i) {
+      const int64_t a = b[i], n = b[i + 1] - b[i];
+      const int64_t n1 = bc[2 * i + 1] - bc[2 * i], n2 = n - n1;
+      DevBuf D, Dl, Dinv;
+      D.alloc(sizeof(float2) * n * n);
+      Dl.alloc(sizeof(float2) * n * n);
+      Dinv.alloc(sizeof(float2) * n * n);
+      dense_block(h, a, n, D.as<float2>(), s);
+      VIE_CUDA(cudaMemcpyAsync(Dl.p, D.p, sizeof(float2) * n * n, cudaMemcpyDeviceToDevice, s));
+      dense_inverse(sol, Dl.as<float2>(), Dinv.as<float2>(), n, s);
+      E[i].alloc(sizeof(float2) * n * n);
+      const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+      float2* Dp = D.as<float2>();
+      float2* Ip = Dinv.as<float2>();
+      float2* Ep = E[i].as<float2>();
+      // E(:, 0:n1) = Dinv(:, 0:n1) D(0:n1, 0:n1);  E(:, n1:n) = Dinv(:, n1:n) D(n1:n, n1:n)
+      VIE_CUBLAS(cublasCgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)n1, (int)n1, &one, (const cuComplex*)Ip,
+                             (int)n, (const cuComplex*)Dp, (int)n, &zero, (cuComplex*)Ep, (int)n));
+      VIE_CUBLAS(cublasCgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)n2, (int)n2, &one,
+                             (const cuComplex*)(Ip + n1 * n), (int)n, (const cuComplex*)(Dp + n1 * n + n1), (int)n,
+                             &zero, (cuComplex*)(Ep + n1 * n), (int)n));
+      sub_identity<<<grid_for(n), 256, 0, s>>>(Ep, n);
+      VIE_CUDA(cudaGetLastError());
+      VIE_CUDA(cudaStreamSynchronize(s));
+      src.refs.push_back(DenseRef{Ep, a, n});
+      specs.push_back(BfSpec{l, i, i, (int)i});
+    }
+    build_program(h, specs, src, h->cfg.tol_fact, P, /*leaf_blocks=*/false, SP_Y, s, res);
+  }
+  h->has_zinv = true;
+}
+
+}  // namespace vie
