@@ -281,7 +281,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "traffic": None,
                          "kernel": "stage_kernel<float,float,1> (all stages of one apply)",
-                         "peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms]},
+                         "peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms],
+                         "stage_gbs": [round(8 * float(e) / (float(t) * 1e6), 1) for e, t in zip(entries, stage_ms)]},
             "e2e": {"value": round(alg_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": round(e2e_ms, 4)},
             "gpu_launches": launches_per_apply * args.steps,

@@ -104,6 +104,64 @@ __device__ __forceinline__ void row_dot_generic(const typename C2<TM>::type* __r
   }
 }
 
+// Single right-hand side, c64 factors and vectors: the bandwidth-bound hot path.
+__global__ void __launch_bounds__(256, 5) stage1_kernel(const OpDesc* __restrict__ ops, const Tile* __restrict__ tiles,
+                                                        int64_t ntiles, const float2* __restrict__ mats,
+                                                        const float2* xt, float2* yt, float2* coef) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp0; t < ntiles; t += nwarps) {
+    const Tile tl = tiles[t];
+    const OpDesc& op = ops[tl.op];
+    const int K = op.K, M = op.M, ld = op.ld;
+    const int g = tl.g, rp = 32 / g;
+    const int li = lane & (g - 1);
+    const float2* x = (op.in_space == SP_X ? xt : (op.in_space == SP_Y ? (const float2*)yt : coef)) + op.in_off;
+    float2* y = (op.out_space == SP_Y ? yt : coef) + op.out_off;
+    const float4* A4 = reinterpret_cast<const float4*>(mats + op.mat_off);
+    const bool acc_mode = op.accumulate != 0;
+    for (int r = tl.r0 + lane / g; r < tl.r0 + tl.nr; r += rp) {
+      float re = 0.f, im = 0.f;
+      if (r < M) {
+        const float4* row = A4 + ((int64_t)r * ld >> 1);
+        for (int k0 = 2 * li; k0 < K; k0 += 8 * g) {
+          float4 a[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + 2 * g * u;
+            a[u] = k < K ? __ldcs(row + (k >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + 2 * g * u;
+            if (k < K) {
+              const float2 x0 = __ldg(x + k);
+              const float2 x1 = (k + 1 < K) ? __ldg(x + k + 1) : make_float2(0.f, 0.f);
+              re = fmaf(a[u].x, x0.x, re); re = fmaf(-a[u].y, x0.y, re);
+              im = fmaf(a[u].x, x0.y, im); im = fmaf(a[u].y, x0.x, im);
+              re = fmaf(a[u].z, x1.x, re); re = fmaf(-a[u].w, x1.y, re);
+              im = fmaf(a[u].z, x1.y, im); im = fmaf(a[u].w, x1.x, im);
+            }
+          }
+        }
+      }
+      for (int o = g >> 1; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (r < M && li == 0) {
+        if (acc_mode) {
+          float2 v = y[r];
+          y[r] = make_float2(v.x + re, v.y + im);
+        } else {
+          y[r] = make_float2(re, im);
+        }
+      }
+    }
+  }
+}
+
 template <class TM, class TV, int NR>
 __global__ void __launch_bounds__(256) stage_kernel(const OpDesc* __restrict__ ops, const Tile* __restrict__ tiles,
                                                     int64_t ntiles, const typename C2<TM>::type* __restrict__ mats,
@@ -228,18 +286,26 @@ void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* 
 // tiles: rows of one op per warp tile, about 16 KB of factor data per tile
 // ---------------------------------------------------------------------------
 void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles) {
+  // g lanes share a row so that each lane streams about four 16-byte vectors
+  // of the row (fewer shuffle rounds per byte, several loads in flight).
+  // Tiles hold up to 16 KB of factor data, less for small stages so that the
+  // launch still has enough warps (152 SMs x 48 warps) to keep HBM busy.
   tiles.clear();
+  int64_t stage_bytes = 0;
+  for (const OpDesc& o : ops) stage_bytes += (int64_t)o.M * o.ld * 8;
+  const int64_t tile_bytes = std::max<int64_t>(2048, std::min<int64_t>(16384, stage_bytes / (152 * 48)));
   for (size_t i = 0; i < ops.size(); ++i) {
     const OpDesc& o = ops[i];
     if (o.M <= 0) continue;
-    int per = (o.K + 1) / 2;  // 16-byte vectors per row for c64
+    const int per = (o.K + 1) / 2;  // 16-byte vectors per row for c64
     int g = 1;
-    while (g < 32 && g < per) g <<= 1;
-    int rp = 32 / g;
-    int64_t row_bytes = (int64_t)o.ld * 8;
-    int64_t passes = std::max<int64_t>(1, 16384 / std::max<int64_t>(1, row_bytes * rp));
-    int nr = int(std::min<int64_t>(passes * rp, (int64_t)((o.M + rp - 1) / rp) * rp));
-    for (int r0 = 0; r0 < o.M; r0 += nr) tiles.push_back(Tile{int32_t(i), r0, std::min(nr, o.M - r0 + (rp - 1)) / rp * rp, g});
+    while (g < 32 && 4 * g < per) g <<= 1;
+    const int rp = 32 / g;
+    const int64_t row_bytes = (int64_t)o.ld * 8;
+    const int64_t passes = std::max<int64_t>(1, tile_bytes / std::max<int64_t>(1, row_bytes * rp));
+    const int nr = int(std::min<int64_t>(passes * rp, (int64_t)((o.M + rp - 1) / rp) * rp));
+    for (int r0 = 0; r0 < o.M; r0 += nr)
+      tiles.push_back(Tile{int32_t(i), r0, (std::min(nr, o.M - r0) + rp - 1) / rp * rp, g});
   }
 }
 
@@ -252,6 +318,14 @@ static void launch_stage(const Stage& st, const void* xt, void* yt, void* coef, 
   const OpDesc* ops = st.ops.as<OpDesc>();
   const Tile* tiles = st.tiles.as<Tile>();
   const typename C2<TM>::type* mats = st.mats.as<typename C2<TM>::type>();
+  if constexpr (sizeof(TM) == 4 && sizeof(TV) == 4) {
+    if (nrhs == 1) {
+      stage1_kernel<<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, (const float2*)mats, (const float2*)xt, (float2*)yt,
+                                         (float2*)coef);
+      VIE_CUDA(cudaGetLastError());
+      return;
+    }
+  }
   for (int r0 = 0; r0 < nrhs;) {
     int left = nrhs - r0;
     if (left >= 8) {
