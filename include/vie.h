@@ -125,6 +125,24 @@ vie_status vie_apply_profile(vie_op* op, int32_t which, const void* X, void* Y, 
 vie_status vie_program_info(const vie_op* op, int32_t which, int64_t* entries, int64_t* bytes,
                             int64_t* tiles, int32_t cap, int32_t* nstages);
 
+/* vie_apply without any device allocation (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory).  cudaMalloc may
+ * synchronize the whole device, which stalls every stream of a latency-bound
+ * serving loop, and a process whose device memory is owned by another
+ * framework's caching allocator has no headroom for allocations made behind
+ * its back.  Same arguments, layout and errors as vie_apply; the work vectors
+ * (tree-ordered X and Y and the butterfly coefficients, 2 N nrhs + C nrhs
+ * complex elements of `dtype`, C the operator's coefficient count) live in one
+ * fixed 64 MiB device array inside the library, held by every GPU that loads
+ * the library until the process exits.  Returns VIE_EINVAL, allocating
+ * nothing, when they do not fit.  The first call on each device looks the
+ * array's device address up (with that device current) and caches it: make
+ * that first call before any stream capture.  All calls on a device share the
+ * array, so calls that overlap on the GPU race on it; order them.  The array
+ * keeps the last call's contents, and no element needs to start at zero. */
+vie_status vie_apply_noalloc(vie_op* op, int32_t which, const void* X, void* Y, int64_t nrhs,
+                             int64_t ldx, int64_t ldy, int32_t dtype, void* stream);
+
 /* out[i] = Z(rows[i], cols[i]) for i < count, evaluated on the GPU in FP64
  * from Eq. (5) (entries of the uncompressed matrix).  rows, cols: device int32
  * face indices in [0, N); out: device c128. */

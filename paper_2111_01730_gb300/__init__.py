@@ -23,7 +23,7 @@ VIE_OP_Z, VIE_OP_ZINV = 0, 1
 VIE_C64, VIE_C128 = 0, 1
 
 # every symbol declared in include/vie.h
-EXPORTS = ["vie_build", "vie_apply", "vie_apply_profile", "vie_program_info", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
+EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
            "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_destroy", "vie_last_error"]
 
 
@@ -69,6 +69,7 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "vie_build": [P, D, P, P, P],
         "vie_apply": [P, I32, P, P, I64, I64, I64, I32, P],
+        "vie_apply_noalloc": [P, I32, P, P, I64, I64, I64, I32, P],
         "vie_entries": [P, P, P, I64, P, P],
         "vie_apply_profile": [P, I32, P, P, I64, I64, I64, I32, P, P, P, I32],
         "vie_program_info": [P, I32, P, P, P, I32, P],
@@ -190,6 +191,15 @@ class Operator:
         _check(_lib.vie_apply(self._h, op, ctypes.c_void_p(Xc.data_ptr()), ctypes.c_void_p(Yc.data_ptr()), nrhs,
                               ldx, ldy, _dtype_code(Xc), _stream_ptr(stream)))
         return Yc[:, 0] if squeeze else Yc
+
+    def apply_noalloc(self, X, Y, op: int = VIE_OP_Z, stream=None):
+        """Y = op X like ``apply``, with the library's fixed work array instead of allocations."""
+        Xc, nrhs, ldx = _colmajor(X, self.n)
+        Yc, _, ldy = _colmajor(Y, self.n)
+        assert Yc.data_ptr() == Y.data_ptr() or Y.dim() == 1, "Y must be column-major"
+        _check(_lib.vie_apply_noalloc(self._h, op, ctypes.c_void_p(Xc.data_ptr()), ctypes.c_void_p(Yc.data_ptr()),
+                                      nrhs, ldx, ldy, _dtype_code(Xc), _stream_ptr(stream)))
+        return Y
 
     def apply_profile(self, X, Y, op: int = VIE_OP_Z, stream=None):
         """Apply with per-kernel CUDA-event times: (ms array [gather, stages..., scatter], launches)."""
