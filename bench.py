@@ -36,6 +36,21 @@ import workloads as W  # noqa: E402
 
 METRIC = "HOD-BF apply GB/s (algorithmic bytes / apply time), single RHS"
 UNIT = "GB/s"
+# DRAM traffic / algorithmic bytes of the single-RHS stage kernel, from the ncu capture in
+# profiles/stage1_kernel_sphere_r1.0.md (stages 1-3 at N = 52,584), scaled to a full apply.
+TRAFFIC_RATIO = 1.021
+TRAFFIC_NOTE = "ncu dram bytes of stage1_kernel stages 1-3 at r=1.0 (N=52,584) = 1.021 x algorithmic, scaled"
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured bf16 dense (burst)"
+    except Exception:
+        return 1900.0, "fallback bf16 dense"
+
+
+BF16_PEAK = _bf16_peak()
 
 
 def peaks():
@@ -175,6 +190,117 @@ def run_reference(args):
     return 0
 
 
+def serving_operators():
+    """Resident scatterers of the serving workload (a reduced set of the eight-operator mix)."""
+    r2 = 1.0 / (10 * 2 ** 0.5)
+    return [W.sphere(0.5, 2.0, r2, name="S1 sphere r=0.5 eps=2"),
+            W.sphere(0.3, 4.0, 1.0 / 20, name="sphere r=0.3 eps=4"),
+            W.shell(0.5, 0.4, -4.0 - 0.3j, 1.0 / 20, name="P2' shell 0.5/0.4 eps=-4-0.3j"),
+            W.sphere(0.3, 10.0, 1.0 / 24, name="sphere r=0.3 eps=10")]
+
+
+def run_serving(args):
+    """Continuous-batching solves (C32 factors, tensor-core multi-column applies, FP64 refinement)
+    against the plain FP64 one-request-at-a-time GPU solver on the same requests."""
+    import torch
+
+    import paper_2111_01730_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    bodies = serving_operators()
+    t0 = time.perf_counter()
+    mixed = [pkg.Operator(b, W.K0, tol_con=1e-3, tol_fact=1e-1, leaf=64, factor_dtype="c64") for b in bodies]
+    build_mixed = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    nreq = args.requests
+    reqs = []
+    for i in range(nreq):
+        op = int(rng.integers(len(mixed)))
+        nr = int(rng.integers(1, 33))
+        k, p = W.planewave_random(nr, seed=1000 + i)
+        reqs.append((op, k, p))
+    rhs = [mixed[op].rhs_planewave(k, p).cpu().numpy() for op, k, p in reqs]
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=nreq))
+    total_rhs = sum(r.shape[1] for r in rhs)
+
+    def serve(sat: bool):
+        srv = pkg.Server(mixed, restart=30, max_iter=300, mem_budget=48 << 30)
+        ids, lat, rels, its = {}, [], [], []
+        torch.cuda.synchronize()
+        start = time.perf_counter()
+        nxt = 0
+        while len(lat) < nreq:
+            now = time.perf_counter() - start
+            while nxt < nreq and (sat or arrivals[nxt] <= now):
+                ids[srv.submit(reqs[nxt][0], rhs[nxt], rtol=1e-3)] = nxt
+                nxt += 1
+            srv.step()
+            for rid in list(ids):
+                i = ids[rid]
+                r = srv.result(rid, mixed[reqs[i][0]].n, rhs[i].shape[1])
+                if r is not None:
+                    lat.append(r[3])
+                    rels.append(r[2].max())
+                    its.append(int(r[1].max()))
+                    del ids[rid]
+        wall = time.perf_counter() - start
+        srv.close()
+        return wall, np.array(lat), np.array(rels), np.array(its)
+
+    serve(True)  # warm-up: tensor-core tiles, workspaces
+    wall_s, lat_s, rel_s, it_s = serve(True)
+    wall_p, lat_p, rel_p, it_p = serve(False)
+    # plain FP64 GPU solver, one request and one right-hand side at a time, on a bounded sample
+    for m in mixed:
+        m.close()
+    fp64 = [pkg.Operator(b, W.K0, tol_con=1e-3, tol_fact=1e-1, leaf=64, factor_dtype="c128") for b in bodies]
+    ns = min(nreq, args.baseline_requests)
+    done_rhs, t_busy, rel_b = 0, 0.0, []
+    for i in range(ns):
+        op, k, p = reqs[i]
+        V = fp64[op].rhs_planewave(k, p)
+        for j in range(V.shape[1]):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            I, it, rel, st = fp64[op].solve(V[:, j:j + 1].contiguous(), rtol=1e-3, restart=30, max_iter=300)
+            torch.cuda.synchronize()
+            t_busy += time.perf_counter() - t1
+            rel_b.append(float(rel.max()))
+            done_rhs += 1
+    base = done_rhs / t_busy
+    line = {"metric": "solves/s (right-hand sides solved per second), continuous batching, rtol 1e-3",
+            "value": round(total_rhs / wall_s, 2), "unit": "solves/s", "higher_is_better": True,
+            "config": {"workload": "; ".join(f"{b.name} (N={m.n})" for b, m in zip(bodies, fp64)),
+                       "requests": nreq, "rhs_total": int(total_rhs), "rhs_per_request": "uniform 1-32",
+                       "chi_con": 1e-3, "chi_fact": 1e-1, "restart": 30, "build_seconds": round(build_mixed, 1)},
+            "saturated": {"solves_per_s": round(total_rhs / wall_s, 2), "p50_s": round(float(np.median(lat_s)), 4),
+                          "p99_s": round(float(np.percentile(lat_s, 99)), 4), "max_relres": float(rel_s.max()),
+                          "max_iters": int(it_s.max())},
+            "poisson": {"rate_req_per_s": args.rate, "solves_per_s": round(total_rhs / wall_p, 2),
+                        "p50_s": round(float(np.median(lat_p)), 4), "p99_s": round(float(np.percentile(lat_p, 99)), 4),
+                        "max_relres": float(rel_p.max())},
+            "plain_fp64_one_at_a_time": {"solves_per_s": round(base, 2), "sample_rhs": done_rhs,
+                                         "max_relres": max(rel_b)},
+            "speedup_vs_plain_fp64": round(total_rhs / wall_s / base, 2)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def job_value(alg_bytes_per_rank: float, total_ms: float, steps: int, world: int, dist=None, device=None):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time.
+
+    Each rank times its own replica; the max over ranks (all_reduce MAX) is the job's time.
+    Returns (GB/s of the job, ms per step of the slowest rank)."""
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / steps
+    return world * alg_bytes_per_rank / (ms_step * 1e-3) / 1e9, ms_step
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,10 +309,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--radius", type=float, default=2.0,
                     help="sphere radius in wavelengths (2.0 = the benchmark workload; smaller for checks/profiles)")
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="right-hand sides per apply (>= 16 runs the tensor-core path)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving benchmark (solves/s, p50/p99 latency)")
+    ap.add_argument("--requests", type=int, default=120)
+    ap.add_argument("--rate", type=float, default=100.0, help="Poisson arrival rate (requests/s) for --serve")
+    ap.add_argument("--baseline-requests", type=int, default=6)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serving(args)
 
     import torch
 
@@ -210,8 +344,12 @@ def main():
     n = op.n
     entries, sbytes, tiles = op.program_info(pkg.VIE_OP_Z)
     E = int(entries.sum())
-    alg_bytes = 8 * E + 16 * n  # per apply, nrhs = 1
-    x = torch.from_numpy(W.random_block(n, 1, seed=7)[:, 0].astype(np.complex64)).cuda()
+    nrhs = args.nrhs
+    alg_bytes = 8 * E + 16 * n * nrhs  # per apply
+    if nrhs == 1:
+        x = torch.from_numpy(W.random_block(n, 1, seed=7)[:, 0].astype(np.complex64)).cuda()
+    else:
+        x = torch.from_numpy(W.random_block(n, nrhs, seed=7).astype(np.complex64)).cuda().t().contiguous().t()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
@@ -240,14 +378,9 @@ def main():
     prof = np.median(np.array(prof), axis=0)
     stage_ms = prof[1:-1]
     launches_per_apply = int(launches)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_step = total_ms / args.steps
-    value = world * alg_bytes / (ms_step * 1e-3) / 1e9
+    value, ms_step = job_value(alg_bytes, total_ms, args.steps, world, dist, "cuda")
     # end to end through the public API: pinned host X -> device, apply, device -> host Y
-    xh = torch.from_numpy(W.random_block(n, 1, seed=8)[:, 0].astype(np.complex64)).pin_memory()
+    xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     xd = torch.empty_like(x)
     for _ in range(3):
@@ -267,27 +400,39 @@ def main():
     # roofline of the dominant kernel: the stage kernel, all its launches of one apply
     stage_alg = 8 * E
     achieved = stage_alg / (stage_ms.sum() * 1e-3) / 1e9
+    useful_tflops = 8.0 * E * nrhs / (stage_ms.sum() * 1e-3) / 1e12
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if nrhs == 1 else METRIC.replace("single RHS", f"{nrhs} RHS"), "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": desc.format(n=n), "n": n, "levels": st.levels, "chi_con": 1e-4, "leaf": 64, "nrhs": 1,
+            "config": {"workload": desc.format(n=n), "n": n, "levels": st.levels, "chi_con": 1e-4, "leaf": 64, "nrhs": nrhs,
                        "factor_entries": E, "factor_bytes_stored": int(sbytes.sum()), "max_rank": st.max_rank,
-                       "build_seconds": round(build_s, 2), "l2": "inputs (factor data) larger than L2, no flush",
+                       "build_seconds": round(build_s, 2),
+                       "build_split_s": {"entries": round(st.build_entries_seconds, 1), "ids": round(st.build_id_seconds, 1),
+                                         "host_sampling": round(st.build_host_seconds, 1)},
+                       "l2": "inputs (factor data) larger than L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "apply_latency_ms": {"p50": round(float(np.percentile(per, 50)), 4),
                                  "p99": round(float(np.percentile(per, 99)), 4)},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "traffic": None,
-                         "kernel": "stage_kernel<float,float,1> (all stages of one apply)",
-                         "peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms],
-                         "stage_gbs": [round(8 * float(e) / (float(t) * 1e6), 1) for e, t in zip(entries, stage_ms)]},
+            "roofline": ({"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(achieved / hbm, 4), "traffic": TRAFFIC_RATIO and round(TRAFFIC_RATIO * stage_alg),
+                          "traffic_note": TRAFFIC_NOTE,
+                          "kernel": "stage1_kernel (single-RHS stages, all launches of one apply)"} if nrhs < 16 else
+                         {"bound": "tensor", "achieved": round(useful_tflops, 2), "peak": BF16_PEAK[0], "unit": "TFLOP/s",
+                          "frac": round(useful_tflops / BF16_PEAK[0], 4), "traffic": None,
+                          "peak_note": BF16_PEAK[1] + "; useful complex flops 8*E*nrhs (the BF16x3 split issues 3x)",
+                          "hbm_gbs": round(achieved, 1),
+                          "kernel": "tc_stage_kernel + stage_kernel remainder (all stages of one apply)"}),
             "e2e": {"value": round(alg_bytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": round(e2e_ms, 4)},
+                    "h2d_bytes_per_step": 8 * n * nrhs, "d2h_bytes_per_step": 8 * n * nrhs,
+                    "ms_per_step": round(e2e_ms, 4)},
             "gpu_launches": launches_per_apply * args.steps,
             "clocks": clk,
         }
+        line["roofline"].update({"peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms],
+                                 "stage_gbs": [round(8 * float(e) / (float(t) * 1e6), 1)
+                                               for e, t in zip(entries, stage_ms)]})
         if not args.no_cpu_baseline and world == 1:
             cb = oracle_apply_sample(15.0)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -90,6 +90,9 @@ typedef struct {
   double invert_seconds;
   int32_t apply_stages_z; /* kernel stages of one Z apply                       */
   int32_t apply_stages_zinv;
+  double build_entries_seconds;  /* of build_seconds: matrix entries on the GPU   */
+  double build_id_seconds;       /* of build_seconds: batched IDs on the GPU      */
+  double build_host_seconds;     /* of build_seconds: row sampling on the host    */
 } vie_stats_t;
 
 /* Build Z (and Zinv when cfg->tol_fact > 0) for the voxel body at wavenumber
@@ -189,6 +192,48 @@ vie_status vie_mesh_host(const vie_voxels* body, int32_t leaf, int64_t* n, int32
 vie_status vie_tree_perm(const vie_op* op, int32_t* perm);
 
 vie_status vie_stats(const vie_op* op, vie_stats_t* out);
+
+/* Waits for `stream` and reports device-side failures of earlier applies:
+ * VIE_ETIMEOUT when a bounded wait inside a tensor-core kernel ran out (the
+ * outputs of that apply are invalid; the flag is cleared), else VIE_OK.
+ * Applies with nrhs >= 16 on c64 vectors and c64 factors run on the tensor
+ * cores (tcgen05, BF16x3 split products, FP32 accumulation); the first such
+ * apply packs the factor tiles (device memory about the size of the factors). */
+vie_status vie_check(vie_op* op, void* stream);
+
+/* ---- serving: continuous batching of solves against resident operators ----
+ * (spec serving loop; the paper's solver phase is Eq. 6 with Zinv.)
+ * A server holds up to `nops` built operators (not owned).  Requests are
+ * admitted while the device memory of their Krylov state (about
+ * N nrhs (restart + 6) 16 bytes) fits `mem_budget`; each vie_server_step
+ * admits what fits, advances every admitted request by one preconditioned
+ * GMRES iteration (the applies of all columns of one operator batched into
+ * one multi-column apply: tensor cores at >= 16 columns), ends restart cycles
+ * with an FP64 refinement residual, and retires finished requests.
+ * Requests submitted between steps join at the next step.  All work runs on
+ * `stream`; every call is synchronous with respect to the host. */
+typedef struct vie_server vie_server;
+
+vie_status vie_server_create(vie_op* const* ops, int32_t nops, int32_t restart, int32_t max_iter,
+                             int64_t mem_budget, void* stream, vie_server** out);
+
+/* Queue a request: V_host is a host c128 N_op x nrhs column-major block (copied
+ * now); *id receives the request id.  VIE_ENAN for NaN/Inf input, VIE_ENOMEM
+ * when one request alone exceeds the budget. */
+vie_status vie_server_submit(vie_server* srv, int32_t op, const void* V_host, int64_t nrhs, double rtol,
+                             int64_t* id);
+
+/* One step; *active / *pending (may be NULL) receive the request counts after it. */
+vie_status vie_server_step(vie_server* srv, int32_t* active, int32_t* pending);
+
+/* Result of a finished request: I_host (host c128 N x nrhs, may be NULL), iters
+ * and relres per column (may be NULL), latency_s = seconds from submit to done.
+ * Returns VIE_ENOTCONV while the request is still queued or running (nothing
+ * written), VIE_EINVAL for an unknown id; a fetched result is released. */
+vie_status vie_server_result(vie_server* srv, int64_t id, void* I_host, int32_t* iters, double* relres,
+                             double* latency_s);
+
+void vie_server_destroy(vie_server* srv);
 
 void vie_destroy(vie_op* op);
 const char* vie_last_error(void);

@@ -24,7 +24,8 @@ VIE_C64, VIE_C128 = 0, 1
 
 # every symbol declared in include/vie.h
 EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
-           "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_destroy", "vie_last_error"]
+           "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_destroy", "vie_last_error",
+           "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy"]
 
 
 class VieError(RuntimeError):
@@ -48,7 +49,9 @@ class Stats(ctypes.Structure):
                 ("max_rank", ctypes.c_int32), ("entries_z", ctypes.c_int64), ("entries_zinv", ctypes.c_int64),
                 ("bytes_z", ctypes.c_int64), ("bytes_zinv", ctypes.c_int64), ("entries_evaluated", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double), ("invert_seconds", ctypes.c_double),
-                ("apply_stages_z", ctypes.c_int32), ("apply_stages_zinv", ctypes.c_int32)]
+                ("apply_stages_z", ctypes.c_int32), ("apply_stages_zinv", ctypes.c_int32),
+                ("build_entries_seconds", ctypes.c_double), ("build_id_seconds", ctypes.c_double),
+                ("build_host_seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,11 +83,18 @@ def load_library(path: str = LIB_PATH):
         "vie_mesh_host": [P, I32, P, P, P, P, P, P],
         "vie_tree_perm": [P, P],
         "vie_stats": [P, P],
+        "vie_check": [P, P],
+        "vie_server_create": [P, I32, I32, I32, I64, P, P],
+        "vie_server_submit": [P, I32, P, I64, D, P],
+        "vie_server_step": [P, P, P],
+        "vie_server_result": [P, I64, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.vie_server_destroy.argtypes = [P]
+    lib.vie_server_destroy.restype = None
     lib.vie_destroy.argtypes = [P]
     lib.vie_destroy.restype = None
     lib.vie_last_error.argtypes = []
@@ -172,6 +182,10 @@ class Operator:
 
     def close(self):
         self.__del__()
+
+    def check(self, stream=None):
+        """Raise VieError(VIE_ETIMEOUT) if a bounded device wait of an earlier apply ran out."""
+        _check(_lib.vie_check(self._h, _stream_ptr(stream)))
 
     def get_stats(self) -> Stats:
         st = Stats()
@@ -278,3 +292,51 @@ class Operator:
         p = np.zeros(self.n, dtype=np.int32)
         _check(_lib.vie_tree_perm(self._h, p.ctypes.data))
         return p
+
+
+class Server:
+    """Continuous-batching solve server over resident operators (vie_server_* in include/vie.h)."""
+
+    def __init__(self, ops, restart: int = 30, max_iter: int = 300, mem_budget: int = 32 << 30, stream=None):
+        lib = load_library()
+        self.ops = list(ops)
+        arr = (ctypes.c_void_p * len(self.ops))(*[o._h.value for o in self.ops])
+        self._h = ctypes.c_void_p()
+        self._keep = arr
+        _check(lib.vie_server_create(arr, len(self.ops), restart, max_iter, int(mem_budget), _stream_ptr(stream),
+                                     ctypes.byref(self._h)))
+
+    def submit(self, op: int, V, rtol: float = 1e-3) -> int:
+        """V: numpy complex128 (N, nrhs) or (N,); returns the request id."""
+        V = np.asarray(V, dtype=np.complex128)
+        if V.ndim == 1:
+            V = V[:, None]
+        Vf = np.asfortranarray(V)
+        rid = ctypes.c_int64(0)
+        _check(_lib.vie_server_submit(self._h, op, Vf.ctypes.data, V.shape[1], float(rtol), ctypes.byref(rid)))
+        return rid.value
+
+    def step(self):
+        a, p = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(_lib.vie_server_step(self._h, ctypes.byref(a), ctypes.byref(p)))
+        return a.value, p.value
+
+    def result(self, rid: int, n: int, nrhs: int):
+        """(I (N, nrhs) complex128, iters, relres, latency_s) or None while the request runs."""
+        I = np.zeros((n, nrhs), dtype=np.complex128, order="F")
+        it = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        lat = ctypes.c_double(0)
+        st = _lib.vie_server_result(self._h, rid, I.ctypes.data, it.ctypes.data, rel.ctypes.data, ctypes.byref(lat))
+        if st == VIE_ENOTCONV:
+            return None
+        _check(st)
+        return I, it, rel, lat.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.vie_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()

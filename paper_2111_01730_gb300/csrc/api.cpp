@@ -37,7 +37,8 @@ void ensure_ws(vie_op* h, const Program& p, int64_t nrhs, int dtype) {
 }
 
 void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dtype, cudaStream_t s) {
-  const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+  Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+  if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, s);
   ensure_ws(h, p, nrhs, dtype);
   program_apply(p, h->perm.as<int32_t>(), X, Y, nrhs, h->mesh.nf, h->mesh.nf, dtype, h->xt.p, h->yt.p, h->coef.p, s);
 }
@@ -114,6 +115,9 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, v
       h->stats.bytes_z = h->z.bytes;
       h->stats.entries_evaluated = br.entries_evaluated;
       h->stats.apply_stages_z = (int32_t)h->z.stages.size();
+      h->stats.build_entries_seconds = br.t_entries;
+      h->stats.build_id_seconds = br.t_id;
+      h->stats.build_host_seconds = br.t_host;
       h->stats.build_seconds = now_s() - t0;
       if (cfg->tol_fact > 0) {
         double t1 = now_s();
@@ -144,7 +148,8 @@ vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t n
     VIE_REQUIRE(dtype == VIE_C64 || dtype == VIE_C128, VIE_EINVAL, "bad dtype");
     VIE_REQUIRE(which == VIE_OP_Z || which == VIE_OP_ZINV, VIE_EINVAL, "bad operator kind");
     VIE_REQUIRE(which == VIE_OP_Z || h->has_zinv, VIE_ENOTSUP, "operator has no inverse (tol_fact <= 0)");
-    const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
     ensure_ws(h, p, nrhs, dtype);
     program_apply(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p,
                   (cudaStream_t)stream);
@@ -158,7 +163,8 @@ vie_status vie_apply_profile(vie_op* h, int32_t which, const void* X, void* Y, i
     VIE_REQUIRE(nrhs >= 1 && ldx >= h->mesh.nf && ldy >= h->mesh.nf, VIE_EINVAL, "bad nrhs or leading dimension");
     VIE_REQUIRE(dtype == VIE_C64 || dtype == VIE_C128, VIE_EINVAL, "bad dtype");
     VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
-    const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
     const int ns = (int)p.stages.size() + 2;
     VIE_REQUIRE(cap >= ns, VIE_EINVAL, "ms array too short (stages + 2 needed)");
     ensure_ws(h, p, nrhs, dtype);
@@ -263,6 +269,22 @@ vie_status vie_tree_perm(const vie_op* h, int32_t* perm) {
   return guarded([&] {
     VIE_REQUIRE(h && perm, VIE_EINVAL, "null argument");
     std::memcpy(perm, h->tree.perm.data(), sizeof(int32_t) * h->mesh.nf);
+  });
+}
+
+vie_status vie_check(vie_op* h, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h, VIE_EINVAL, "null operator");
+    for (Program* p : {&h->z, &h->zinv}) {
+      if (!p->err.p) continue;
+      int e = 0;
+      VIE_CUDA(cudaMemcpyAsync(&e, p->err.p, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+      VIE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+      if (e) {
+        VIE_CUDA(cudaMemsetAsync(p->err.p, 0, sizeof(int), (cudaStream_t)stream));
+        throw Error{VIE_ETIMEOUT, "a bounded wait in the tensor-core apply ran out; its output is invalid"};
+      }
+    }
   });
 }
 

@@ -310,17 +310,25 @@ void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles) {
 }
 
 template <class TM, class TV>
+static void launch_tiles(const Stage& st, const OpDesc* ops, const Tile* tiles, int64_t ntiles, const void* xt,
+                         void* yt, void* coef, int nrhs, cudaStream_t s);
+
+template <class TM, class TV>
 static void launch_stage(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, cudaStream_t s) {
+  launch_tiles<TM, TV>(st, st.ops.as<OpDesc>(), st.tiles.as<Tile>(), st.ntiles, xt, yt, coef, nrhs, s);
+}
+
+template <class TM, class TV>
+static void launch_tiles(const Stage& st, const OpDesc* ops, const Tile* tiles, int64_t ntiles, const void* xt,
+                         void* yt, void* coef, int nrhs, cudaStream_t s) {
   using V2 = typename C2<TV>::type;
-  if (st.ntiles == 0) return;
-  int64_t blocks = (st.ntiles + 7) / 8;
+  if (ntiles == 0) return;
+  int64_t blocks = (ntiles + 7) / 8;
   int grid = (int)std::min<int64_t>(blocks, 152 * 16);
-  const OpDesc* ops = st.ops.as<OpDesc>();
-  const Tile* tiles = st.tiles.as<Tile>();
   const typename C2<TM>::type* mats = st.mats.as<typename C2<TM>::type>();
   if constexpr (sizeof(TM) == 4 && sizeof(TV) == 4) {
     if (nrhs == 1) {
-      stage1_kernel<<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, (const float2*)mats, (const float2*)xt, (float2*)yt,
+      stage1_kernel<<<grid, 256, 0, s>>>(ops, tiles, ntiles, (const float2*)mats, (const float2*)xt, (float2*)yt,
                                          (float2*)coef);
       VIE_CUDA(cudaGetLastError());
       return;
@@ -329,16 +337,16 @@ static void launch_stage(const Stage& st, const void* xt, void* yt, void* coef, 
   for (int r0 = 0; r0 < nrhs;) {
     int left = nrhs - r0;
     if (left >= 8) {
-      stage_kernel<TM, TV, 8><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      stage_kernel<TM, TV, 8><<<grid, 256, 0, s>>>(ops, tiles, ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
       r0 += 8;
     } else if (left >= 4) {
-      stage_kernel<TM, TV, 4><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      stage_kernel<TM, TV, 4><<<grid, 256, 0, s>>>(ops, tiles, ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
       r0 += 4;
     } else if (left >= 2) {
-      stage_kernel<TM, TV, 2><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      stage_kernel<TM, TV, 2><<<grid, 256, 0, s>>>(ops, tiles, ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
       r0 += 2;
     } else {
-      stage_kernel<TM, TV, 1><<<grid, 256, 0, s>>>(ops, tiles, st.ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
+      stage_kernel<TM, TV, 1><<<grid, 256, 0, s>>>(ops, tiles, ntiles, mats, (const V2*)xt, (V2*)yt, (V2*)coef, nrhs, r0);
       r0 += 1;
     }
     VIE_CUDA(cudaGetLastError());
@@ -356,9 +364,18 @@ static void run_program(const Program& p, const int32_t* perm, const void* X, vo
   gather_kernel<TV><<<grid, 256, 0, s>>>(perm, p.n, (int)nrhs, (const V2*)X, ldx, (V2*)xt);
   VIE_CUDA(cudaGetLastError());
   if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+  const bool tc = p.tc_ready && sizeof(TV) == 4 && p.factor_dtype == VIE_C64 && nrhs >= kTcMinRhs;
   for (const Stage& st : p.stages) {
-    if (p.factor_dtype == VIE_C64) launch_stage<float, TV>(st, xt, yt, coef, (int)nrhs, s);
-    else launch_stage<double, TV>(st, xt, yt, coef, (int)nrhs, s);
+    if (tc) {
+      // dense blocks on the tensor cores, the small ones on the SIMT kernel
+      tc_launch(st, xt, yt, coef, (int)nrhs, p.err.as<int>(), s);
+      launch_tiles<float, TV>(st, st.rest_ops.as<OpDesc>(), st.rest_tiles.as<Tile>(), st.rest_ntiles, xt, yt, coef,
+                              (int)nrhs, s);
+    } else if (p.factor_dtype == VIE_C64) {
+      launch_stage<float, TV>(st, xt, yt, coef, (int)nrhs, s);
+    } else {
+      launch_stage<double, TV>(st, xt, yt, coef, (int)nrhs, s);
+    }
     if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
   }
   scatter_kernel<TV><<<grid, 256, 0, s>>>(perm, p.n, (int)nrhs, (const V2*)yt, (V2*)Y, ldy);
@@ -370,6 +387,14 @@ void program_apply(const Program& p, const int32_t* d_perm, const void* X, void*
                    int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s, cudaEvent_t* ev) {
   if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
   else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
+}
+
+void program_prepare_tc(Program& p, cudaStream_t s) {
+  if (p.tc_ready || p.factor_dtype != VIE_C64) return;
+  p.err.alloc(sizeof(int));
+  VIE_CUDA(cudaMemsetAsync(p.err.p, 0, sizeof(int), s));
+  for (Stage& st : p.stages) tc_prepare_stage(st, st.host_ops, s);
+  p.tc_ready = true;
 }
 
 int64_t program_launches(const Program& p, int64_t nrhs) {

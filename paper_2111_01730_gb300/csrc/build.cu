@@ -166,6 +166,7 @@ static void finalize_stage(Stage& st, const std::vector<OpDesc>& ops, std::vecto
     VIE_CUDA(cudaMemcpyAsync(st.tiles.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
   st.entries = 0;
   for (auto& o : ops) st.entries += (int64_t)o.M * o.K;
+  st.host_ops = ops;
   st.bytes = tot * elem_bytes;
   VIE_CUDA(cudaStreamSynchronize(s));
   for (auto& c : chunks) c.release();
@@ -288,6 +289,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
       }
     }
     // row samples of the ID jobs (independent per job, deterministic per seed)
+    const auto th0 = std::chrono::steady_clock::now();
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t q = 0; q < (int64_t)jobs.size(); ++q) {
       Job& j = jobs[q];
@@ -302,6 +304,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
       uint64_t key = ((uint64_t)j.bf << 40) ^ ((uint64_t)j.k << 32) ^ (uint64_t)j.blk;
       smp.rows(tlev, tidx, nlev, nidx, (int)j.cols.size(), key, j.rows);
     }
+    res.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - th0).count();
     // ---- process in chunks ----
     std::vector<OpDesc> ops;
     std::vector<DevBuf> chunks;
@@ -342,7 +345,10 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
       std::vector<int32_t> srcs(nj);
       for (int q = 0; q < nj; ++q)  // leaf blocks carry their leaf index as the source
         srcs[q] = jobs[q0 + q].bf >= 0 ? bfs[jobs[q0 + q].bf].src : (int32_t)jobs[q0 + q].blk;
+      const auto te0 = std::chrono::steady_clock::now();
       src.eval(eb, prefix, rows, cols, srcs, aoff, dA.as<double2>(), s);
+      VIE_CUDA(cudaStreamSynchronize(s));
+      res.t_entries += std::chrono::duration<double>(std::chrono::steady_clock::now() - te0).count();
       // IDs
       std::vector<IdJob> ij;
       std::vector<int> ij_q;
@@ -366,8 +372,11 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
         dpiv.alloc(sizeof(int32_t) * std::max<int64_t>(1, poff));
         drank.alloc(sizeof(int32_t) * ij.size());
         VIE_CUDA(cudaMemcpyAsync(dij.p, ij.data(), sizeof(IdJob) * ij.size(), cudaMemcpyHostToDevice, s));
+        const auto ti0 = std::chrono::steady_clock::now();
         id_batched(dij.as<IdJob>(), (int)ij.size(), maxn, dA.as<double2>(), dV.as<double2>(), dpiv.as<int32_t>(),
                    drank.as<int32_t>(), tol_id, s);
+        VIE_CUDA(cudaStreamSynchronize(s));
+        res.t_id += std::chrono::duration<double>(std::chrono::steady_clock::now() - ti0).count();
         VIE_CUDA(cudaMemcpyAsync(piv.data(), dpiv.p, sizeof(int32_t) * poff, cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaMemcpyAsync(rk.data(), drank.p, sizeof(int32_t) * ij.size(), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaStreamSynchronize(s));

@@ -280,7 +280,49 @@ __device__ double2 far_scalar(const EntryCtx& c, const Elem& A, const Elem& B) {
   return s;
 }
 
+// far tier in FP32 (used by the HOD-BF builder): the 4-point rules of both tets, relative
+// coordinates, FP32 kernel evaluations; the result is accurate to ~1e-6 relative.
+struct F3 { float x, y, z; };
+__device__ __forceinline__ F3 f3_point(int p, int i, int ox, int oy, int oz, float h) {
+  F3 r{0.f, 0.f, 0.f};
+  for (int a = 0; a < 4; ++a) {
+    const float l = (float)c_tet4[i][a];
+    r.x += l * (float)(ox + c_kuhn[p][a][0]) * h;
+    r.y += l * (float)(oy + c_kuhn[p][a][1]) * h;
+    r.z += l * (float)(oz + c_kuhn[p][a][2]) * h;
+  }
+  return r;
+}
+
+__device__ void far_tet_pair_f32(const EntryCtx& c, int pa, int pb, int dx, int dy, int dz, V3 qa, V3 qb,
+                                 double2& sum, double2& sumv) {
+  const float h = (float)c.h, k0 = (float)c.k0, w = (float)(0.25 * c.h * c.h * c.h / 6.0);
+  float sr = 0.f, si = 0.f, vr = 0.f, vi = 0.f;
+  F3 rj[4];
+  for (int j = 0; j < 4; ++j) rj[j] = f3_point(pb, j, dx, dy, dz, h);
+  for (int i = 0; i < 4; ++i) {
+    const F3 ri = f3_point(pa, i, 0, 0, 0, h);
+    const float ax = ri.x - (float)qa.x, ay = ri.y - (float)qa.y, az = ri.z - (float)qa.z;
+    for (int j = 0; j < 4; ++j) {
+      const float ex = ri.x - rj[j].x, ey = ri.y - rj[j].y, ez = ri.z - rj[j].z;
+      const float R = sqrtf(ex * ex + ey * ey + ez * ez);
+      float sn, cs;
+      sincosf(k0 * R, &sn, &cs);
+      const float f = (float)kInv4Pi * w * w / R;
+      const float gr = cs * f, gi = -sn * f;
+      sr += gr;
+      si += gi;
+      const float d = ax * (rj[j].x - (float)qb.x) + ay * (rj[j].y - (float)qb.y) + az * (rj[j].z - (float)qb.z);
+      vr += gr * d;
+      vi += gi * d;
+    }
+  }
+  sum = make_double2(sr, si);
+  sumv = make_double2(vr, vi);
+}
+
 // contribution of the tet pair (T, a) x (T', b) to Z(m, n)
+template <bool FAR32>
 __device__ double2 tet_pair(const EntryCtx& c, int T, int a, double sa, int Tp, int b, double sb) {
   const TetDev tA = c.tets[T], tB = c.tets[Tp];
   const int dx = tB.vx - tA.vx, dy = tB.vy - tA.vy, dz = tB.vz - tA.vz;
@@ -304,6 +346,11 @@ __device__ double2 tet_pair(const EntryCtx& c, int T, int a, double sa, int Tp, 
                              M2.y - qbM1.y - qaM1p.y + dot(qa, qb) * M0.y);
     Avec = cscale(I, ca * cb);
     Phi = M0;
+  } else if (FAR32) {
+    double2 s, sv;
+    far_tet_pair_f32(c, tA.type, tB.type, dx, dy, dz, qa, qb, s, sv);
+    Avec = cscale(sv, ca * cb);
+    Phi = s;
   } else {
     Elem EA{tA.type, -1, 0, 0, 0}, EB{tB.type, -1, dx, dy, dz};
     double2 s = make_double2(0, 0), sv = make_double2(0, 0);
@@ -346,6 +393,7 @@ __device__ double2 pair_scalar(const EntryCtx& c, int T, int fa, int Tp, int fb)
   return far_scalar(c, Elem{tA.type, fa, 0, 0, 0}, Elem{tB.type, fb, dx, dy, dz});
 }
 
+template <bool FAR32>
 __device__ double2 entry(const EntryCtx& c, int m, int n) {
   const FaceDev Fm = c.faces[m], Fn = c.faces[n];
   const double h = c.h, vol = h * h * h / 6.0;
@@ -356,7 +404,7 @@ __device__ double2 entry(const EntryCtx& c, int m, int n) {
     if (Tm[i] < 0) continue;
     for (int j = 0; j < 2; ++j) {
       if (Tn[j] < 0) continue;
-      z = cadd(z, tet_pair(c, Tm[i], Am[i], i == 0 ? 1.0 : -1.0, Tn[j], Bn[j], j == 0 ? 1.0 : -1.0));
+      z = cadd(z, tet_pair<FAR32>(c, Tm[i], Am[i], i == 0 ? 1.0 : -1.0, Tn[j], Bn[j], j == 0 ? 1.0 : -1.0));
     }
   }
   const double2 jump = make_double2(Fn.jump_re, Fn.jump_im);
@@ -391,9 +439,10 @@ __device__ double2 entry(const EntryCtx& c, int m, int n) {
 __global__ void entries_pairs_kernel(EntryCtx c, const int32_t* rows, const int32_t* cols, int64_t count,
                                      double2* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = entry(c, rows[i], cols[i]);
+    out[i] = entry<false>(c, rows[i], cols[i]);
 }
 
+template <bool FAR32>
 __global__ void entries_blocks_kernel(EntryCtx c, const EntryBlock* blocks, const int64_t* prefix, int nblocks,
                                       int64_t total, const int32_t* rows, const int32_t* cols, double2* out) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
@@ -405,7 +454,7 @@ __global__ void entries_blocks_kernel(EntryCtx c, const EntryBlock* blocks, cons
     const EntryBlock b = blocks[lo];
     int64_t k = g - prefix[lo];
     int i = int(k % b.m), j = int(k / b.m);
-    out[b.out_off + k] = entry(c, rows[b.row_off + i], cols[b.col_off + j]);
+    out[b.out_off + k] = entry<FAR32>(c, rows[b.row_off + i], cols[b.col_off + j]);
   }
 }
 
@@ -608,7 +657,8 @@ void entries_blocks(const Geometry& g, const EntryBlock* d_blocks, const int64_t
                     int64_t total, const int32_t* d_rows, const int32_t* d_cols, double2* d_out, cudaStream_t s) {
   if (total <= 0 || nblocks <= 0) return;
   int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  entries_blocks_kernel<<<grid, 256, 0, s>>>(ctx(g), d_blocks, d_prefix, nblocks, total, d_rows, d_cols, d_out);
+  // the builder evaluates far-tier volume pairs in FP32 (near/mid tables and surface terms stay FP64)
+  entries_blocks_kernel<true><<<grid, 256, 0, s>>>(ctx(g), d_blocks, d_prefix, nblocks, total, d_rows, d_cols, d_out);
   VIE_CUDA(cudaGetLastError());
 }
 

@@ -171,11 +171,23 @@ struct Tile {            // a warp's unit of work: rows [r0, r0 + nr) of op `op`
   int32_t op, r0, nr, g; // g = lanes per row (power of two)
 };
 
+// A tensor-core work item: output rows [m0, m0 + mc) of one stage block, all of K.
+struct TcItem {
+  int64_t mat_off, b_off, in_off, out_off;  // c64 source offset, bf16 tile byte offset
+  int32_t ld, K, m0, mc, n;                 // n = mc rounded up to 16 (the MMA's N)
+  int16_t in_space, out_space;
+  int32_t accumulate;
+};
+
 struct Stage {
   DevBuf mats;           // packed factor matrices (c64 or c128)
   DevBuf ops;            // OpDesc[nops]
   DevBuf tiles;          // Tile[ntiles]
   int64_t nops = 0, ntiles = 0, entries = 0, bytes = 0;
+  std::vector<OpDesc> host_ops;  // kept for the tensor-core preparation
+  // tensor-core (multi-RHS) form, prepared on first use
+  DevBuf tc_tiles, tc_ops, rest_ops, rest_tiles;
+  int64_t tc_items = 0, tc_bytes = 0, rest_ntiles = 0;
 };
 
 struct Program {         // one operator's apply: gather, stages, scatter
@@ -183,13 +195,23 @@ struct Program {         // one operator's apply: gather, stages, scatter
   int64_t n = 0, ncoef = 0;
   int factor_dtype = VIE_C64;
   int64_t entries = 0, bytes = 0;
+  bool tc_ready = false;
+  DevBuf err;            // device int: a bounded wait in a tensor-core kernel ran out
 };
+
+// tensor-core multi-RHS path (tc.cu)
+bool tc_eligible(const OpDesc& o);
+void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s);
+void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* d_err, cudaStream_t s);
+size_t tc_smem_bytes();
+constexpr int kTcMinRhs = 16;   // the tensor-core path serves nrhs >= 16 (c64 factors and vectors)
 
 void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles);
 void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs,
                    int64_t ldx, int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c,
                    cudaStream_t s, cudaEvent_t* events = nullptr);
 int64_t program_launches(const Program& p, int64_t nrhs);
+void program_prepare_tc(Program& p, cudaStream_t s);
 void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* d_src_ld,
                    const int32_t* d_src_colmajor, const int64_t* d_dst_off, const int32_t* d_M,
                    const int32_t* d_K, const int32_t* d_ld, int nmat, void* dst, int dst_dtype,
@@ -199,6 +221,7 @@ struct BuildResult {
   int64_t entries_evaluated = 0;
   int64_t leaf_entries = 0;
   int max_rank = 0;
+  double t_entries = 0, t_id = 0, t_host = 0;  // seconds (entries incl. transfers, batched IDs, host sampling)
 };
 
 // Where the builder takes matrix entries from (tree positions in, c128 col-major blocks out).

@@ -4,7 +4,8 @@
 // used here is right preconditioning, Z M u = r, x = M u, with M = Zinv when
 // the operator carries one, so that the stopping test is on the true residual.
 // Precision split: every application of Z or Zinv inside the Krylov loop runs
-// on complex FP32 vectors (C32 factors, FP32 accumulation); the Arnoldi basis,
+// on complex FP32 vectors (C32 factors, FP32 accumulation) -- or on FP64
+// vectors when the operator stores FP64 factors (the plain FP64 solver); the Arnoldi basis,
 // its classical Gram-Schmidt (applied twice) orthogonalization and the Givens
 // least squares are FP64; the outer refinement residual r = b - Z x applies
 // the same C32 factors with FP64 vectors and accumulation.
@@ -161,8 +162,10 @@ void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, doub
   ws.V.alloc(sizeof(double2) * nb * ldb);
   VIE_CUDA(cudaMemsetAsync(ws.V.p, 0, sizeof(double2) * nb * ldb, s));
   ws.w.alloc(sizeof(double2) * nb);
-  ws.t64a.alloc(sizeof(float2) * nb);
-  ws.t64b.alloc(sizeof(float2) * nb);
+  // operators with FP64 factors solve in FP64 throughout (the plain FP64 path)
+  const bool fp64 = h->cfg.factor_dtype == VIE_C128;
+  ws.t64a.alloc((fp64 ? sizeof(double2) : sizeof(float2)) * nb);
+  ws.t64b.alloc((fp64 ? sizeof(double2) : sizeof(float2)) * nb);
   ws.h.alloc(sizeof(double2) * nrhs * ldh);
   ws.y.alloc(sizeof(double2) * nrhs * ldh);
   ws.nrm.alloc(sizeof(double) * nrhs);
@@ -234,16 +237,28 @@ void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, doub
       for (int c = 0; c < nrhs; ++c) any_live |= live[c] != 0;
       if (!any_live) break;
       // w = Z M v_k
-      gather_basis<<<G, 256, 0, s>>>(V, n, ldb, k, (int)nrhs, ws.tmp.as<double2>());
-      to_c64<<<G, 256, 0, s>>>(ws.tmp.as<double2>(), va, nb);
-      if (pre) {
-        op_apply(h, VIE_OP_ZINV, va, vb, nrhs, VIE_C64, s);
-        op_apply(h, VIE_OP_Z, vb, va, nrhs, VIE_C64, s);
+      if (fp64) {
+        double2* da = ws.t64a.as<double2>();
+        double2* db = ws.t64b.as<double2>();
+        gather_basis<<<G, 256, 0, s>>>(V, n, ldb, k, (int)nrhs, da);
+        if (pre) {
+          op_apply(h, VIE_OP_ZINV, da, db, nrhs, VIE_C128, s);
+          op_apply(h, VIE_OP_Z, db, w, nrhs, VIE_C128, s);
+        } else {
+          op_apply(h, VIE_OP_Z, da, w, nrhs, VIE_C128, s);
+        }
       } else {
-        op_apply(h, VIE_OP_Z, va, vb, nrhs, VIE_C64, s);
-        std::swap(va, vb);
+        gather_basis<<<G, 256, 0, s>>>(V, n, ldb, k, (int)nrhs, ws.tmp.as<double2>());
+        to_c64<<<G, 256, 0, s>>>(ws.tmp.as<double2>(), va, nb);
+        if (pre) {
+          op_apply(h, VIE_OP_ZINV, va, vb, nrhs, VIE_C64, s);
+          op_apply(h, VIE_OP_Z, vb, va, nrhs, VIE_C64, s);
+        } else {
+          op_apply(h, VIE_OP_Z, va, vb, nrhs, VIE_C64, s);
+          std::swap(va, vb);
+        }
+        to_c128<<<G, 256, 0, s>>>(va, w, nb);
       }
-      to_c128<<<G, 256, 0, s>>>(va, w, nb);
       // classical Gram-Schmidt, twice
       for (int pass = 0; pass < 2; ++pass) {
         dots<<<(int)nrhs * (k + 1), 256, 0, s>>>(V, n, ldb, w, k + 1, ws.h.as<double2>(), ldh);
@@ -301,7 +316,10 @@ void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, doub
     }
     VIE_CUDA(cudaMemcpyAsync(ws.y.p, yv.data(), sizeof(double2) * nrhs * ldh, cudaMemcpyHostToDevice, s));
     combine<<<G, 256, 0, s>>>(V, n, ldb, m, ws.y.as<double2>(), ldh, (int)nrhs, ws.d.as<double2>());
-    if (pre) {
+    if (pre && fp64) {
+      op_apply(h, VIE_OP_ZINV, ws.d.p, ws.tmp.p, nrhs, VIE_C128, s);
+      VIE_CUDA(cudaMemcpyAsync(ws.d.p, ws.tmp.p, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
+    } else if (pre) {
       to_c64<<<G, 256, 0, s>>>(ws.d.as<double2>(), va, nb);
       op_apply(h, VIE_OP_ZINV, va, vb, nrhs, VIE_C64, s);
       to_c128<<<G, 256, 0, s>>>(vb, ws.d.as<double2>(), nb);

@@ -1,0 +1,351 @@
+// Multi-RHS HOD-BF apply on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// With many right-hand sides every stage block Y_blk = A X_blk (A: M x K complex)
+// is a dense contraction.  It runs transposed, Y^T (nrhs x M) = X^T (nrhs x K) A^T,
+// so that the MMA's M dimension (128) is the right-hand-side count and the
+// butterfly rank M only sets the MMA's N (a multiple of 16).  The complex
+// product is split into four real products (the 4M form),
+//   Yr^T = Xr^T Ar^T - Xi^T Ai^T,   Yi^T = Xr^T Ai^T + Xi^T Ar^T,
+// with the minus sign carried by the instruction's negate-A bit, and each real
+// product runs as three BF16 products with FP32 accumulation in TMEM
+// (a = a_hi + a_lo, a_hi b_hi + a_hi b_lo + a_lo b_hi), which keeps about 16
+// mantissa bits of the FP32 factors.
+//
+// Data movement: the factor blocks of the operator are packed once into
+// per-(block, 128-row chunk, 32-column chunk) tiles of [Ar_hi|Ar_lo|Ai_hi|Ai_lo]
+// bf16 in the canonical no-swizzle K-major core-matrix layout and copied into
+// shared memory with one bulk asynchronous copy (cp.async.bulk, completion on an
+// mbarrier) per k-chunk; the coefficient vectors X are converted to the same
+// layout by the CTA's threads.  Two shared-memory buffers overlap the copies and
+// conversions of chunk k+1 with the MMAs of chunk k.  One thread issues the
+// MMAs; the four warps drain TMEM with tcgen05.ld and write the outputs.
+// Blocks too small to fill a tile stay on the SIMT path (stage_kernel).
+//
+// Every wait on an mbarrier is bounded; a CTA that gives up records the event in
+// an error flag that the host reads after the apply.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace vie {
+
+namespace {
+
+constexpr int kKc = 32;        // complex columns (K) per chunk
+constexpr int kRows = 128;     // right-hand sides per MMA (M of the instruction)
+constexpr int kMaxN = 128;     // output rows per work item (N of the instruction)
+constexpr int kThreads = 128;  // four warps: one TMEM lane quarter each
+constexpr int kTileA = 4 * kRows * kKc * 2;   // bytes: Xr_hi, Xr_lo, Xi_hi, Xi_lo
+constexpr int kTileBMax = 4 * kMaxN * kKc * 2;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// canonical K-major no-swizzle layout: element (r, k) of an R x 32 bf16 tile
+__device__ __forceinline__ int cm_index(int r, int k) { return ((r >> 3) * (kKc / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  // start address, leading byte offset (next core matrix along K) = 128 B,
+  // stride byte offset (next 8-row group) = 4 core matrices = 512 B, version 1, no swizzle
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ uint32_t instr_desc(int n, int neg_a) {
+  uint32_t d = 0;
+  d |= 1u << 4;   // accumulate in F32
+  d |= 1u << 7;   // A: BF16
+  d |= 1u << 10;  // B: BF16
+  d |= (uint32_t)neg_a << 13;
+  d |= (uint32_t)(n >> 3) << 17;
+  d |= (uint32_t)(kRows >> 4) << 24;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t taddr, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+               :: "r"(taddr), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// packing: c64 row-major block rows [m0, m0+Mc) -> bf16 tiles per 32-column chunk
+// ---------------------------------------------------------------------------
+__global__ void tc_pack_kernel(const TcItem* items, int nitems, const float2* mats, __nv_bfloat16* out) {
+  const TcItem it = items[blockIdx.x];
+  const int nk = (it.K + kKc - 1) / kKc;
+  const int64_t tile = (int64_t)4 * it.n * kKc;  // bf16 elements per k-chunk tile
+  for (int64_t e = threadIdx.x; e < (int64_t)nk * it.n * kKc; e += blockDim.x) {
+    const int kc = int(e / (it.n * kKc));
+    const int rem = int(e % (it.n * kKc));
+    const int r = rem / kKc, k = rem % kKc;
+    const int kk = kc * kKc + k;
+    float2 a = make_float2(0.f, 0.f);
+    if (r < it.mc && kk < it.K) a = mats[it.mat_off + (int64_t)(it.m0 + r) * it.ld + kk];
+    __nv_bfloat16 rh, rl, ih, il;
+    split_bf16(a.x, rh, rl);
+    split_bf16(a.y, ih, il);
+    __nv_bfloat16* t = out + it.b_off / 2 + kc * tile;
+    const int ci = cm_index(r, k);
+    const int64_t part = (int64_t)it.n * kKc;
+    t[ci] = rh;
+    t[part + ci] = rl;
+    t[2 * part + ci] = ih;
+    t[3 * part + ci] = il;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the tensor-core stage kernel (persistent over work items)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(const TcItem* __restrict__ items, int nitems,
+                                                                const uint8_t* __restrict__ btiles,
+                                                                const float2* xt, float2* yt, float2* coef,
+                                                                int nrhs, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA[2] = {smem, smem + kTileA};
+  uint8_t* sB[2] = {smem + 2 * kTileA, smem + 2 * kTileA + kTileBMax};
+  __shared__ __align__(8) uint64_t load_bar[2], mma_bar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&load_bar[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mma_bar[b])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;  // D_r: columns [0, 128), D_i: [128, 256)
+  uint32_t load_phase[2] = {0, 0}, mma_phase[2] = {0, 0};
+  bool ok = true;
+  const int nrc = (nrhs + kRows - 1) / kRows;
+  for (int w = blockIdx.x; w < nitems * nrc && ok; w += gridDim.x) {
+    const TcItem it = items[w / nrc];
+    const int r0 = (w % nrc) * kRows;
+    const int nk = (it.K + kKc - 1) / kKc;
+    const float2* x = (it.in_space == SP_X ? xt : (it.in_space == SP_Y ? (const float2*)yt : coef)) +
+                      (int64_t)it.in_off * nrhs;
+    const uint32_t tile_bytes = 4u * it.n * kKc * 2u;
+    const uint32_t id_n = (uint32_t)it.n;
+    int pending[2] = {0, 0};
+    for (int kc = 0; kc < nk && ok; ++kc) {
+      const int b = kc & 1;
+      if (pending[b]) {  // the MMAs that read this buffer two chunks ago must be done
+        ok = mbar_wait(smem_u32(&mma_bar[b]), mma_phase[b]);
+        mma_phase[b] ^= 1;
+        pending[b] = 0;
+      }
+      if (tid == 0 && ok) {
+        const uint32_t bar = smem_u32(&load_bar[b]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(tile_bytes) : "memory");
+        const uint8_t* src = btiles + it.b_off + (int64_t)kc * tile_bytes;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(sB[b])), "l"(src), "r"(tile_bytes), "r"(bar) : "memory");
+      }
+      // X chunk -> bf16 hi/lo tiles (rows = right-hand sides, columns = k)
+      __nv_bfloat16* a = reinterpret_cast<__nv_bfloat16*>(sA[b]);
+      constexpr int part = kRows * kKc;
+      for (int e = tid; e < kRows * kKc; e += kThreads) {
+        const int k = e / kRows, r = e % kRows;  // consecutive threads: consecutive rhs
+        const int kk = kc * kKc + k, rr = r0 + r;
+        float2 v = make_float2(0.f, 0.f);
+        if (kk < it.K && rr < nrhs) v = x[(int64_t)kk * nrhs + rr];
+        __nv_bfloat16 h, l;
+        const int ci = cm_index(r, k);
+        split_bf16(v.x, h, l);
+        a[ci] = h;
+        a[part + ci] = l;
+        split_bf16(v.y, h, l);
+        a[2 * part + ci] = h;
+        a[3 * part + ci] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0 && ok) {
+        ok = mbar_wait(smem_u32(&load_bar[b]), load_phase[b]);
+        load_phase[b] ^= 1;
+        if (ok) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t A0 = smem_u32(sA[b]), B0 = smem_u32(sB[b]);
+          const uint32_t pa = (uint32_t)part * 2u, pb = id_n * kKc * 2u;  // bytes per hi/lo part
+          const uint32_t Xrh = A0, Xrl = A0 + pa, Xih = A0 + 2 * pa, Xil = A0 + 3 * pa;
+          const uint32_t Arh = B0, Arl = B0 + pb, Aih = B0 + 2 * pb, Ail = B0 + 3 * pb;
+          const uint32_t idp = instr_desc(it.n, 0), idm = instr_desc(it.n, 1);
+          const uint32_t Dr = tmem, Di = tmem + 128;
+          for (int ks = 0; ks < kKc / 16; ++ks) {
+            const uint32_t o = ks * 256;  // two core matrices along K
+            const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+            // Dr += Xr Ar - Xi Ai ; Di += Xr Ai + Xi Ar  (each as hi*hi + hi*lo + lo*hi)
+            mma_bf16(Dr, smem_desc(Xrh + o), smem_desc(Arh + o), idp, acc0);
+            mma_bf16(Dr, smem_desc(Xrh + o), smem_desc(Arl + o), idp, 1);
+            mma_bf16(Dr, smem_desc(Xrl + o), smem_desc(Arh + o), idp, 1);
+            mma_bf16(Dr, smem_desc(Xih + o), smem_desc(Aih + o), idm, 1);
+            mma_bf16(Dr, smem_desc(Xih + o), smem_desc(Ail + o), idm, 1);
+            mma_bf16(Dr, smem_desc(Xil + o), smem_desc(Aih + o), idm, 1);
+            mma_bf16(Di, smem_desc(Xrh + o), smem_desc(Aih + o), idp, acc0);
+            mma_bf16(Di, smem_desc(Xrh + o), smem_desc(Ail + o), idp, 1);
+            mma_bf16(Di, smem_desc(Xrl + o), smem_desc(Aih + o), idp, 1);
+            mma_bf16(Di, smem_desc(Xih + o), smem_desc(Arh + o), idp, 1);
+            mma_bf16(Di, smem_desc(Xih + o), smem_desc(Arl + o), idp, 1);
+            mma_bf16(Di, smem_desc(Xil + o), smem_desc(Arh + o), idp, 1);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       :: "r"(smem_u32(&mma_bar[b])) : "memory");
+        }
+      }
+      // every thread tracks the commit of this buffer
+      pending[b] = 1;
+      __syncthreads();
+      ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    }
+    // drain: wait for the outstanding commits (the last one covers all MMAs issued before it)
+    for (int b = 0; b < 2 && ok; ++b)
+      if (pending[b]) {
+        ok = mbar_wait(smem_u32(&mma_bar[b]), mma_phase[b]);
+        mma_phase[b] ^= 1;
+        pending[b] = 0;
+      }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // epilogue: warp w owns TMEM lanes (right-hand sides) 32w .. 32w+31
+    float2* y = (it.out_space == SP_Y ? yt : coef) + (int64_t)it.out_off * nrhs;
+    const int rr = r0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < it.n; c0 += 8) {
+      uint32_t vr[8], vi[8];
+      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7])
+                   : "r"(lane_addr));
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7])
+                   : "r"(lane_addr + 128));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (rr < nrhs) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int m = c0 + j;
+          if (m < it.mc) {
+            float2* dst = y + (int64_t)(it.m0 + m) * nrhs + rr;
+            const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
+            if (it.accumulate) {
+              float2 o = *dst;
+              *dst = make_float2(o.x + re, o.y + im);
+            } else {
+              *dst = make_float2(re, im);
+            }
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t tc_smem_bytes() { return 2 * (size_t)kTileA + 2 * (size_t)kTileBMax + 1024; }
+
+bool tc_eligible(const OpDesc& o) { return o.M >= 16 && o.K >= 32; }
+
+void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s) {
+  // split eligible ops into 128-row work items and pack their bf16 tiles
+  std::vector<TcItem> items;
+  int64_t off = 0;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const OpDesc& o = ops[i];
+    if (!tc_eligible(o)) continue;
+    for (int m0 = 0; m0 < o.M; m0 += kMaxN) {
+      TcItem t{};
+      t.mat_off = o.mat_off;
+      t.ld = o.ld;
+      t.K = o.K;
+      t.m0 = m0;
+      t.mc = std::min(kMaxN, o.M - m0);
+      t.n = (t.mc + 15) / 16 * 16;
+      t.in_off = o.in_off;
+      t.out_off = o.out_off;
+      t.in_space = o.in_space;
+      t.out_space = o.out_space;
+      t.accumulate = o.accumulate;
+      t.b_off = off;
+      off += (int64_t)((o.K + kKc - 1) / kKc) * 4 * t.n * kKc * 2;
+      items.push_back(t);
+    }
+  }
+  st.tc_items = (int64_t)items.size();
+  st.tc_bytes = off;
+  if (!items.empty()) {
+    st.tc_tiles.alloc(off);
+    st.tc_ops.alloc(sizeof(TcItem) * items.size());
+    VIE_CUDA(cudaMemcpyAsync(st.tc_ops.p, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice, s));
+    tc_pack_kernel<<<(int)items.size(), 256, 0, s>>>(st.tc_ops.as<TcItem>(), (int)items.size(), st.mats.as<float2>(),
+                                                     st.tc_tiles.as<__nv_bfloat16>());
+    VIE_CUDA(cudaGetLastError());
+  }
+  // the SIMT remainder: ops that are not eligible (a stage may have no eligible op at all)
+  std::vector<OpDesc> rest;
+  for (const OpDesc& o : ops)
+    if (!tc_eligible(o)) rest.push_back(o);
+  std::vector<Tile> tiles;
+  make_tiles(rest, tiles);
+  st.rest_ops.alloc(sizeof(OpDesc) * std::max<size_t>(1, rest.size()));
+  st.rest_tiles.alloc(sizeof(Tile) * std::max<size_t>(1, tiles.size()));
+  if (!rest.empty())
+    VIE_CUDA(cudaMemcpyAsync(st.rest_ops.p, rest.data(), sizeof(OpDesc) * rest.size(), cudaMemcpyHostToDevice, s));
+  if (!tiles.empty())
+    VIE_CUDA(cudaMemcpyAsync(st.rest_tiles.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
+  st.rest_ntiles = (int64_t)tiles.size();
+  VIE_CUDA(cudaStreamSynchronize(s));
+}
+
+void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* d_err, cudaStream_t s) {
+  if (st.tc_items == 0) return;
+  static bool attr = false;
+  if (!attr) {
+    VIE_CUDA(cudaFuncSetAttribute(tc_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
+    attr = true;
+  }
+  const int nrc = (nrhs + kRows - 1) / kRows;
+  const int64_t work = st.tc_items * nrc;
+  const int grid = (int)std::min<int64_t>(work, 152);
+  tc_stage_kernel<<<grid, kThreads, tc_smem_bytes(), s>>>(st.tc_ops.as<TcItem>(), (int)st.tc_items,
+                                                          st.tc_tiles.as<uint8_t>(), (const float2*)xt, (float2*)yt,
+                                                          (float2*)coef, nrhs, d_err);
+  VIE_CUDA(cudaGetLastError());
+}
+
+}  // namespace vie

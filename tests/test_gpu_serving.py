@@ -1,0 +1,87 @@
+"""Serving: continuous batching of preconditioned solves; each result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2111_01730_gb300 as pkg  # noqa: E402
+from oracle.dense import solve_dense  # noqa: E402
+from oracle.entries import rhs_planewave  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ops(lossy_sphere):
+    a = pkg.Operator(lossy_sphere["body"], W.K0, tol_con=1e-5, tol_fact=1e-1, leaf=64)
+    b = pkg.Operator(W.shell(0.22, 0.12, W.drude_eps(), 1.0 / 20), W.K0, tol_con=1e-5, tol_fact=1e-2, leaf=64)
+    return a, b
+
+
+def _run(srv, ids, n_of, nrhs_of, max_steps=2000):
+    out = {}
+    for _ in range(max_steps):
+        srv.step()
+        for rid in ids:
+            if rid in out:
+                continue
+            r = srv.result(rid, n_of[rid], nrhs_of[rid])
+            if r is not None:
+                out[rid] = r
+        if len(out) == len(ids):
+            return out
+    raise AssertionError("requests did not finish")
+
+
+def test_same_result_alone_and_in_the_mix(ops, lossy_sphere):
+    a, b = ops
+    ka, pa = W.planewave_random(3, seed=31)
+    Va = a.rhs_planewave(ka, pa).cpu().numpy()
+    srv = pkg.Server([a, b], restart=30, max_iter=300, mem_budget=8 << 30)
+    rid = srv.submit(0, Va, rtol=1e-3)
+    alone = _run(srv, [rid], {rid: a.n}, {rid: 3})[rid]
+    assert np.all(alone[2] <= 1e-3)
+    # the same request in a mix of concurrent requests on two operators (20 columns: tensor-core applies)
+    kb, pb = W.planewave_random(5, seed=32)
+    Vb = b.rhs_planewave(kb, pb).cpu().numpy()
+    kc, pc = W.planewave_random(20, seed=33)
+    Vc = a.rhs_planewave(kc, pc).cpu().numpy()
+    r1 = srv.submit(1, Vb, rtol=1e-3)
+    r0 = srv.submit(0, Va, rtol=1e-3)
+    srv.step()                      # r1, r0 on the GPU ...
+    r2 = srv.submit(0, Vc, rtol=1e-3)  # ... when r2 arrives; it joins the next step
+    res = _run(srv, [r0, r1, r2], {r0: a.n, r1: b.n, r2: a.n}, {r0: 3, r1: 5, r2: 20})
+    for r in res.values():
+        assert np.all(r[2] <= 1e-3) and r[3] > 0
+    mix = res[r0]
+    diff = np.linalg.norm(mix[0] - alone[0]) / np.linalg.norm(alone[0])
+    assert diff <= 2e-3, diff
+    # and both against the dense LU solution of the oracle
+    Io = solve_dense(lossy_sphere["Z"], rhs_planewave(lossy_sphere["E"], ka, pa))
+    for r in (alone, mix):
+        assert np.linalg.norm(r[0] - Io) / np.linalg.norm(Io) <= 5e-3
+    srv.close()
+
+
+def test_admission_by_krylov_memory(ops):
+    a, _ = ops
+    k, p = W.planewave_random(2, seed=41)
+    V = a.rhs_planewave(k, p).cpu().numpy()
+    need = a.n * 2 * 16 * (10 + 6) + 4096
+    srv = pkg.Server([a], restart=10, max_iter=200, mem_budget=int(need * 1.5))
+    r0 = srv.submit(0, V)
+    r1 = srv.submit(0, V)
+    active, pending = srv.step()
+    assert active == 1 and pending == 1    # the second request waits for memory
+    res = _run(srv, [r0, r1], {r0: a.n, r1: a.n}, {r0: 2, r1: 2})
+    assert res[r1][3] > res[r0][3]
+    bad = V.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(pkg.VieError) as e:
+        srv.submit(0, bad)
+    assert e.value.status == pkg.VIE_ENAN
+    srv.close()
