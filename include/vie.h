@@ -93,6 +93,9 @@ typedef struct {
   double build_entries_seconds;  /* of build_seconds: matrix entries on the GPU   */
   double build_id_seconds;       /* of build_seconds: batched IDs on the GPU      */
   double build_host_seconds;     /* of build_seconds: row sampling on the host    */
+  int32_t zinv_top_level;        /* Zinv holds Algorithm 1's levels l >= this one (0 = all);
+                                    nodes larger than 32,768 unknowns are not inverted   */
+  int32_t reserved2;
 } vie_stats_t;
 
 /* Build Z (and Zinv when cfg->tol_fact > 0) for the voxel body at wavenumber
@@ -145,6 +148,20 @@ vie_status vie_program_info(const vie_op* op, int32_t which, int64_t* entries, i
  * keeps the last call's contents, and no element needs to start at zero. */
 vie_status vie_apply_noalloc(vie_op* op, int32_t which, const void* X, void* Y, int64_t nrhs,
                              int64_t ldx, int64_t ldy, int32_t dtype, void* stream);
+
+/* Autotune the single-RHS apply (c64 factors): for every stage, time each
+ * candidate tiling (maximum tile 4, 16 or 64 KB of factor data x 2, 4 or 8
+ * 16-byte vectors per lane and row) with CUDA events on `stream` and keep the
+ * fastest.  choice (host, cap >= stages, may be NULL) receives the index of the
+ * chosen candidate per stage (tile-size index * 3 + vector index).  Results of
+ * later applies are unchanged (tiling only moves work between warps). */
+vie_status vie_autotune(vie_op* op, int32_t which, int32_t* choice, int32_t cap, void* stream);
+
+/* Block shapes of one stage of an apply program (introspection for profiling):
+ * *count receives the number of blocks; M[i], K[i] (host, may be NULL) their
+ * rows and columns for i < min(count, cap). */
+vie_status vie_program_blocks(const vie_op* op, int32_t which, int32_t stage, int32_t* M, int32_t* K,
+                              int64_t cap, int64_t* count);
 
 /* out[i] = Z(rows[i], cols[i]) for i < count, evaluated on the GPU in FP64
  * from Eq. (5) (entries of the uncompressed matrix).  rows, cols: device int32

@@ -23,7 +23,7 @@ VIE_OP_Z, VIE_OP_ZINV = 0, 1
 VIE_C64, VIE_C128 = 0, 1
 
 # every symbol declared in include/vie.h
-EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
+EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
            "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_destroy", "vie_last_error",
            "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy"]
 
@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("build_seconds", ctypes.c_double), ("invert_seconds", ctypes.c_double),
                 ("apply_stages_z", ctypes.c_int32), ("apply_stages_zinv", ctypes.c_int32),
                 ("build_entries_seconds", ctypes.c_double), ("build_id_seconds", ctypes.c_double),
-                ("build_host_seconds", ctypes.c_double)]
+                ("build_host_seconds", ctypes.c_double), ("zinv_top_level", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +77,8 @@ def load_library(path: str = LIB_PATH):
         "vie_entries": [P, P, P, I64, P, P],
         "vie_apply_profile": [P, I32, P, P, I64, I64, I64, I32, P, P, P, I32],
         "vie_program_info": [P, I32, P, P, P, I32, P],
+        "vie_program_blocks": [P, I32, I32, P, P, I64, P],
+        "vie_autotune": [P, I32, P, I32, P],
         "vie_rhs_planewave": [P, P, P, I64, P, P],
         "vie_solve": [P, P, P, I64, D, I32, I32, P, P, P],
         "vie_farfield": [P, P, I64, P, I64, P, P],
@@ -235,6 +238,21 @@ class Operator:
         ns = ctypes.c_int32(0)
         _check(_lib.vie_program_info(self._h, op, e.ctypes.data, b.ctypes.data, t.ctypes.data, 64, ctypes.byref(ns)))
         return e[:ns.value], b[:ns.value], t[:ns.value]
+
+    def autotune(self, op: int = VIE_OP_Z, stream=None):
+        """Tune the single-RHS stage tiling; returns the chosen candidate index per stage."""
+        ch = np.zeros(64, dtype=np.int32)
+        _check(_lib.vie_autotune(self._h, op, ch.ctypes.data, 64, _stream_ptr(stream)))
+        return ch[: self.program_info(op)[0].size]
+
+    def program_blocks(self, op: int, stage: int):
+        """(M, K) int32 arrays of the blocks of one stage."""
+        cnt = ctypes.c_int64(0)
+        _check(_lib.vie_program_blocks(self._h, op, stage, None, None, 0, ctypes.byref(cnt)))
+        M = np.zeros(cnt.value, dtype=np.int32)
+        K = np.zeros(cnt.value, dtype=np.int32)
+        _check(_lib.vie_program_blocks(self._h, op, stage, M.ctypes.data, K.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return M, K
 
     def entries(self, rows, cols, stream=None):
         """Z(rows[i], cols[i]) in FP64 (int32 CUDA tensors) -> complex128 CUDA tensor."""

@@ -40,7 +40,8 @@ void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dt
   Program& p = which == VIE_OP_Z ? h->z : h->zinv;
   if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, s);
   ensure_ws(h, p, nrhs, dtype);
-  program_apply(p, h->perm.as<int32_t>(), X, Y, nrhs, h->mesh.nf, h->mesh.nf, dtype, h->xt.p, h->yt.p, h->coef.p, s);
+  program_apply_graph(p, h->perm.as<int32_t>(), X, Y, nrhs, h->mesh.nf, h->mesh.nf, dtype, h->xt.p, h->yt.p,
+                      h->coef.p, s);
 }
 
 }  // namespace vie
@@ -129,6 +130,7 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, v
         h->stats.apply_stages_zinv = (int32_t)h->zinv.stages.size();
         h->stats.max_rank = std::max(h->stats.max_rank, bi.max_rank);
         h->stats.invert_seconds = now_s() - t1;
+        h->stats.zinv_top_level = h->zinv_top_level;
       }
     } catch (...) {
       delete h;
@@ -151,8 +153,8 @@ vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t n
     Program& p = which == VIE_OP_Z ? h->z : h->zinv;
     if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
     ensure_ws(h, p, nrhs, dtype);
-    program_apply(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p,
-                  (cudaStream_t)stream);
+    program_apply_graph(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p,
+                        (cudaStream_t)stream);
   });
 }
 
@@ -200,6 +202,36 @@ vie_status vie_program_info(const vie_op* h, int32_t which, int64_t* entries, in
       if (bytes) bytes[i] = p.stages[i].bytes;
       if (launches) launches[i] = p.stages[i].ntiles;
     }
+  });
+}
+
+vie_status vie_program_blocks(const vie_op* h, int32_t which, int32_t stage, int32_t* M, int32_t* K, int64_t cap,
+                              int64_t* count) {
+  return guarded([&] {
+    VIE_REQUIRE(h && count, VIE_EINVAL, "null argument");
+    VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
+    const Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    VIE_REQUIRE(stage >= 0 && stage < (int)p.stages.size(), VIE_EINVAL, "stage out of range");
+    const auto& ops = p.stages[stage].host_ops;
+    *count = (int64_t)ops.size();
+    for (int64_t i = 0; i < (int64_t)ops.size() && i < cap; ++i) {
+      if (M) M[i] = ops[i].M;
+      if (K) K[i] = ops[i].K;
+    }
+  });
+}
+
+vie_status vie_autotune(vie_op* h, int32_t which, int32_t* choice, int32_t cap, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h, VIE_EINVAL, "null operator");
+    VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
+    Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    VIE_REQUIRE(!choice || cap >= (int32_t)p.stages.size(), VIE_EINVAL, "choice array too short");
+    ensure_ws(h, p, 1, VIE_C64);
+    VIE_CUDA(cudaMemsetAsync(h->xt.p, 0, h->xt.bytes, (cudaStream_t)stream));
+    VIE_CUDA(cudaMemsetAsync(h->yt.p, 0, h->yt.bytes, (cudaStream_t)stream));
+    VIE_CUDA(cudaMemsetAsync(h->coef.p, 0, h->coef.bytes, (cudaStream_t)stream));
+    program_autotune(p, h->xt.p, h->yt.p, h->coef.p, (cudaStream_t)stream, choice);
   });
 }
 

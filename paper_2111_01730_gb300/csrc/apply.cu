@@ -285,21 +285,23 @@ void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* 
 // ---------------------------------------------------------------------------
 // tiles: rows of one op per warp tile, about 16 KB of factor data per tile
 // ---------------------------------------------------------------------------
-void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles) {
-  // g lanes share a row so that each lane streams about four 16-byte vectors
-  // of the row (fewer shuffle rounds per byte, several loads in flight).
-  // Tiles hold up to 16 KB of factor data, less for small stages so that the
-  // launch still has enough warps (152 SMs x 48 warps) to keep HBM busy.
+void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles) { make_tiles(ops, tiles, 16384, 4); }
+
+void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles, int64_t max_tile_bytes, int vec_target) {
+  // g lanes share a row so that each lane streams about `vec_target` 16-byte
+  // vectors of the row (fewer shuffle rounds per byte, several loads in flight).
+  // Tiles hold up to max_tile_bytes of factor data, less for small stages so that
+  // the launch still has enough warps (152 SMs x 48 warps) to keep HBM busy.
   tiles.clear();
   int64_t stage_bytes = 0;
   for (const OpDesc& o : ops) stage_bytes += (int64_t)o.M * o.ld * 8;
-  const int64_t tile_bytes = std::max<int64_t>(2048, std::min<int64_t>(16384, stage_bytes / (152 * 48)));
+  const int64_t tile_bytes = std::max<int64_t>(2048, std::min<int64_t>(max_tile_bytes, stage_bytes / (152 * 48)));
   for (size_t i = 0; i < ops.size(); ++i) {
     const OpDesc& o = ops[i];
     if (o.M <= 0) continue;
     const int per = (o.K + 1) / 2;  // 16-byte vectors per row for c64
     int g = 1;
-    while (g < 32 && 4 * g < per) g <<= 1;
+    while (g < 32 && vec_target * g < per) g <<= 1;
     const int rp = 32 / g;
     const int64_t row_bytes = (int64_t)o.ld * 8;
     const int64_t passes = std::max<int64_t>(1, tile_bytes / std::max<int64_t>(1, row_bytes * rp));
@@ -354,8 +356,13 @@ static void launch_tiles(const Stage& st, const OpDesc* ops, const Tile* tiles, 
 }
 
 template <class TV>
+static void run_stages(const Program& p, int64_t nrhs, void* xt, void* yt, void* coef, cudaStream_t s,
+                       cudaEvent_t* ev, int& e);
+
+template <class TV>
 static void run_program(const Program& p, const int32_t* perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
-                        int64_t ldy, void* xt, void* yt, void* coef, cudaStream_t s, cudaEvent_t* ev) {
+                        int64_t ldy, void* xt, void* yt, void* coef, cudaStream_t s, cudaEvent_t* ev,
+                        cudaGraphExec_t graph = nullptr) {
   using V2 = typename C2<TV>::type;
   const int64_t tot = p.n * nrhs;
   const int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
@@ -364,6 +371,16 @@ static void run_program(const Program& p, const int32_t* perm, const void* X, vo
   gather_kernel<TV><<<grid, 256, 0, s>>>(perm, p.n, (int)nrhs, (const V2*)X, ldx, (V2*)xt);
   VIE_CUDA(cudaGetLastError());
   if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+  if (graph) VIE_CUDA(cudaGraphLaunch(graph, s));
+  else run_stages<TV>(p, nrhs, xt, yt, coef, s, ev, e);
+  scatter_kernel<TV><<<grid, 256, 0, s>>>(perm, p.n, (int)nrhs, (const V2*)yt, (V2*)Y, ldy);
+  VIE_CUDA(cudaGetLastError());
+  if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+}
+
+template <class TV>
+static void run_stages(const Program& p, int64_t nrhs, void* xt, void* yt, void* coef, cudaStream_t s,
+                       cudaEvent_t* ev, int& e) {
   const bool tc = p.tc_ready && sizeof(TV) == 4 && p.factor_dtype == VIE_C64 && nrhs >= kTcMinRhs;
   for (const Stage& st : p.stages) {
     if (tc) {
@@ -378,15 +395,91 @@ static void run_program(const Program& p, const int32_t* perm, const void* X, vo
     }
     if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
   }
-  scatter_kernel<TV><<<grid, 256, 0, s>>>(perm, p.n, (int)nrhs, (const V2*)yt, (V2*)Y, ldy);
-  VIE_CUDA(cudaGetLastError());
-  if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
+}
+
+void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
+                         int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s) {
+  const bool tc = p.tc_ready && dtype == VIE_C64 && p.factor_dtype == VIE_C64 && nrhs >= kTcMinRhs;
+  if (!p.graph || p.g_nrhs != nrhs || p.g_dtype != dtype || p.g_xt != d_xt || p.g_yt != d_yt || p.g_coef != d_c ||
+      p.g_tc != tc) {
+    if (p.graph) { cudaGraphExecDestroy(p.graph); p.graph = nullptr; }
+    if (!p.capture_stream) VIE_CUDA(cudaStreamCreateWithFlags(&p.capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    VIE_CUDA(cudaStreamBeginCapture(p.capture_stream, cudaStreamCaptureModeThreadLocal));
+    int e = 0;
+    try {
+      if (dtype == VIE_C64) run_stages<float>(p, nrhs, d_xt, d_yt, d_c, p.capture_stream, nullptr, e);
+      else run_stages<double>(p, nrhs, d_xt, d_yt, d_c, p.capture_stream, nullptr, e);
+    } catch (...) {
+      cudaStreamEndCapture(p.capture_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    VIE_CUDA(cudaStreamEndCapture(p.capture_stream, &g));
+    cudaError_t ie = cudaGraphInstantiate(&p.graph, g, 0);
+    cudaGraphDestroy(g);
+    VIE_CUDA(ie);
+    p.g_nrhs = nrhs; p.g_dtype = dtype; p.g_xt = d_xt; p.g_yt = d_yt; p.g_coef = d_c; p.g_tc = tc;
+  }
+  if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, p.graph);
+  else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, p.graph);
 }
 
 void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
                    int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s, cudaEvent_t* ev) {
   if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
   else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
+}
+
+// Autotuner of the single-RHS stage kernel: per stage, time every (tile size,
+// vectors per lane) candidate with CUDA events and keep the fastest tiles.
+int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s, int32_t* choice) {
+  if (p.factor_dtype != VIE_C64) return 0;
+  static const int64_t kTileCand[] = {4096, 16384, 65536};
+  static const int kVecCand[] = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  VIE_CUDA(cudaEventCreate(&e0));
+  VIE_CUDA(cudaEventCreate(&e1));
+  int nst = 0;
+  for (Stage& st : p.stages) {
+    if (st.host_ops.empty()) { ++nst; continue; }
+    float best = 1e30f;
+    std::vector<Tile> best_tiles;
+    int best_c = 0, c = 0;
+    for (int64_t tb : kTileCand)
+      for (int vt : kVecCand) {
+        std::vector<Tile> tiles;
+        make_tiles(st.host_ops, tiles, tb, vt);
+        DevBuf dt;
+        dt.alloc(sizeof(Tile) * std::max<size_t>(1, tiles.size()));
+        VIE_CUDA(cudaMemcpyAsync(dt.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
+        const int64_t nt = (int64_t)tiles.size();
+        const int grid = (int)std::min<int64_t>((nt + 7) / 8, 152 * 16);
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          VIE_CUDA(cudaEventRecord(e0, s));
+          stage1_kernel<<<grid, 256, 0, s>>>(st.ops.as<OpDesc>(), dt.as<Tile>(), nt, st.mats.as<float2>(),
+                                             (const float2*)xt, (float2*)yt, (float2*)coef);
+          VIE_CUDA(cudaEventRecord(e1, s));
+          VIE_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          VIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep > 0) tmin = std::min(tmin, ms);
+        }
+        if (tmin < best) { best = tmin; best_tiles = tiles; best_c = c; }
+        ++c;
+      }
+    st.tiles.alloc(sizeof(Tile) * std::max<size_t>(1, best_tiles.size()));
+    VIE_CUDA(cudaMemcpyAsync(st.tiles.p, best_tiles.data(), sizeof(Tile) * best_tiles.size(), cudaMemcpyHostToDevice, s));
+    st.ntiles = (int64_t)best_tiles.size();
+    if (choice) choice[nst] = best_c;
+    ++nst;
+  }
+  VIE_CUDA(cudaStreamSynchronize(s));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (p.graph) { cudaGraphExecDestroy(p.graph); p.graph = nullptr; }  // tiles changed
+  return nst;
 }
 
 void program_prepare_tc(Program& p, cudaStream_t s) {

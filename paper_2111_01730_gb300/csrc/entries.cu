@@ -436,10 +436,11 @@ __device__ double2 entry(const EntryCtx& c, int m, int n) {
   return z;
 }
 
+template <bool FAR32>
 __global__ void entries_pairs_kernel(EntryCtx c, const int32_t* rows, const int32_t* cols, int64_t count,
                                      double2* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = entry<false>(c, rows[i], cols[i]);
+    out[i] = entry<FAR32>(c, rows[i], cols[i]);
 }
 
 template <bool FAR32>
@@ -646,10 +647,11 @@ static EntryCtx ctx(const Geometry& g) {
 }
 
 void entries_pairs(const Geometry& g, const int32_t* rows, const int32_t* cols, int64_t count, double2* out,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool far32) {
   if (count <= 0) return;
   int grid = (int)std::min<int64_t>((count + 255) / 256, 152 * 16);
-  entries_pairs_kernel<<<grid, 256, 0, s>>>(ctx(g), rows, cols, count, out);
+  if (far32) entries_pairs_kernel<true><<<grid, 256, 0, s>>>(ctx(g), rows, cols, count, out);
+  else entries_pairs_kernel<false><<<grid, 256, 0, s>>>(ctx(g), rows, cols, count, out);
   VIE_CUDA(cudaGetLastError());
 }
 

@@ -135,7 +135,7 @@ void entries_blocks(const Geometry& g, const EntryBlock* d_blocks, const int64_t
                     int nblocks, int64_t total, const int32_t* d_rows, const int32_t* d_cols,
                     double2* d_out, cudaStream_t s);
 void entries_pairs(const Geometry& g, const int32_t* rows, const int32_t* cols, int64_t count,
-                   double2* out, cudaStream_t s);
+                   double2* out, cudaStream_t s, bool far32 = false);
 void rhs_planewave(const Geometry& g, const double* khat, const double* pol, int nrhs, double2* V,
                    cudaStream_t s);
 void farfield(const Geometry& g, const double2* I, int nrhs, const double* dirs, int ndir,
@@ -171,12 +171,23 @@ struct Tile {            // a warp's unit of work: rows [r0, r0 + nr) of op `op`
   int32_t op, r0, nr, g; // g = lanes per row (power of two)
 };
 
-// A tensor-core work item: output rows [m0, m0 + mc) of one stage block, all of K.
+// A tensor-core work item: up to 64 output rows taken from up to kTcMaxSeg
+// blocks of one stage that read the same input slice (so the slice is converted
+// once for all of them).
+constexpr int kTcMaxSeg = 8;
+struct TcSeg {
+  int64_t mat_off, out_off;  // c64 matrix offset, output row offset of the block
+  int32_t ld, row0;          // block row stride; first block row in this item
+  int32_t rows, start;       // rows taken; first item row they occupy
+  int16_t out_space, accumulate;
+  int32_t pad;
+};
 struct TcItem {
-  int64_t mat_off, b_off, in_off, out_off;  // c64 source offset, bf16 tile byte offset
-  int32_t ld, K, m0, mc, n;                 // n = mc rounded up to 16 (the MMA's N)
-  int16_t in_space, out_space;
-  int32_t accumulate;
+  int64_t b_off, in_off;     // bf16 tile byte offset; input row offset
+  int32_t K, n, mc, nseg;    // K columns, n = mc rounded up to 16 (the MMA's N), mc rows
+  int16_t in_space, pad16;
+  int32_t pad;
+  TcSeg seg[kTcMaxSeg];
 };
 
 struct Stage {
@@ -197,6 +208,21 @@ struct Program {         // one operator's apply: gather, stages, scatter
   int64_t entries = 0, bytes = 0;
   bool tc_ready = false;
   DevBuf err;            // device int: a bounded wait in a tensor-core kernel ran out
+  // CUDA graph of the stage launches (the gather and scatter stay outside: they
+  // touch the caller's X and Y); rebuilt when nrhs, dtype or workspaces change
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int64_t g_nrhs = -1;
+  int g_dtype = -1;
+  const void *g_xt = nullptr, *g_yt = nullptr, *g_coef = nullptr;
+  bool g_tc = false;
+  Program() = default;
+  Program(const Program&) = delete;
+  Program& operator=(const Program&) = delete;
+  ~Program() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+  }
 };
 
 // tensor-core multi-RHS path (tc.cu)
@@ -204,14 +230,20 @@ bool tc_eligible(const OpDesc& o);
 void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s);
 void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* d_err, cudaStream_t s);
 size_t tc_smem_bytes();
-constexpr int kTcMinRhs = 16;   // the tensor-core path serves nrhs >= 16 (c64 factors and vectors)
+constexpr int kTcMinRhs = 16;
+constexpr int64_t kDenseInverseLimit = 32768;  // largest diagonal block formed densely by the inverse builder   // the tensor-core path serves nrhs >= 16 (c64 factors and vectors)
 
 void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles);
+void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles, int64_t max_tile_bytes, int vec_target);
 void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs,
                    int64_t ldx, int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c,
                    cudaStream_t s, cudaEvent_t* events = nullptr);
+// same, with the stage launches replayed from a cached CUDA graph
+void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
+                         int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s);
 int64_t program_launches(const Program& p, int64_t nrhs);
 void program_prepare_tc(Program& p, cudaStream_t s);
+int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s, int32_t* choice);
 void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* d_src_ld,
                    const int32_t* d_src_colmajor, const int64_t* d_dst_off, const int32_t* d_M,
                    const int32_t* d_K, const int32_t* d_ld, int nmat, void* dst, int dst_dtype,
@@ -271,6 +303,7 @@ struct vie_op {
   vie::DevBuf tet_faces; // int32 4*nt
   vie::Program z, zinv;
   bool has_zinv = false;
+  int zinv_top_level = 0;   // Algorithm 1 levels l >= this are in Zinv
   vie::DevBuf xt, yt, coef;  // apply workspaces (grown on demand)
   size_t ws_bytes = 0;
   vie_config cfg{};

@@ -14,7 +14,9 @@
 // compressed by the same ID-based butterfly construction as Z (Eqs. 7-10),
 // reading its entries from the dense matrix.  This replaces the randomized
 // recompression (BF_random_matvec inside BF_SMW, Algorithm 2) and is limited
-// by the dense top-level block (N^2 complex FP32 entries held three times).
+// by the dense blocks: levels whose nodes hold more than kDenseInverseLimit
+// unknowns are skipped, so that for large N the inverse is exact to chi_fact
+// inside the subtrees below that level and block diagonal above it.
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
@@ -126,7 +128,7 @@ void dense_block(vie_op* h, int64_t a, int64_t n, float2* D, cudaStream_t s) {
       for (int64_t i = 0; i < n; ++i) { pr[j * n + i] = r[i]; pc[j * n + i] = r[c0 + j]; }
     VIE_CUDA(cudaMemcpyAsync(prow.p, pr.data(), sizeof(int32_t) * n * nc, cudaMemcpyHostToDevice, s));
     VIE_CUDA(cudaMemcpyAsync(cols.p, pc.data(), sizeof(int32_t) * n * nc, cudaMemcpyHostToDevice, s));
-    entries_pairs(h->geo, prow.as<int32_t>(), cols.as<int32_t>(), n * nc, tmp.as<double2>(), s);
+    entries_pairs(h->geo, prow.as<int32_t>(), cols.as<int32_t>(), n * nc, tmp.as<double2>(), s, /*far32=*/true);
     c128_to_c64<<<grid_for(n * nc), 256, 0, s>>>(tmp.as<double2>(), D + c0 * n, n * nc);
     VIE_CUDA(cudaGetLastError());
     VIE_CUDA(cudaStreamSynchronize(s));
@@ -158,8 +160,16 @@ void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
   const Tree& t = h->tree;
   const int LH = t.levels;
   const int64_t N = h->mesh.nf;
-  VIE_REQUIRE((double)N * (double)N * 8.0 * 3.0 < 200e9, VIE_ENOTSUP,
-              "dense inverse construction limited to about 90k unknowns");
+  // Levels whose diagonal blocks exceed the dense limit are left out: the inverse
+  // then stops at level l_min (block diagonal over the level-l_min subtrees).
+  int l_min = 0;
+  while (l_min < LH) {
+    int64_t big = 0;
+    for (size_t i = 0; i + 1 < t.bounds[l_min].size(); ++i) big = std::max<int64_t>(big, t.bounds[l_min][i + 1] - t.bounds[l_min][i]);
+    if (big <= kDenseInverseLimit) break;
+    ++l_min;
+  }
+  h->zinv_top_level = l_min;
   cusolverDnHandle_t sol = nullptr;
   cublasHandle_t blas = nullptr;
   VIE_CUSOLVER(cusolverDnCreate(&sol));
@@ -192,7 +202,7 @@ void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
     build_program(h, {}, src, h->cfg.tol_fact, P, /*leaf_blocks=*/true, SP_X, s, res);
   }
   // levels L_H - 1 .. 0: E_tau = D_tau^-1 diag(D_tau1, D_tau2) - I, compressed at chi_fact
-  for (int l = LH - 1; l >= 0; --l) {
+  for (int l = LH - 1; l >= l_min; --l) {
     const auto& b = t.bounds[l];
     const auto& bc = t.bounds[l + 1];
     const int64_t nn = (int64_t)b.size() - 1;

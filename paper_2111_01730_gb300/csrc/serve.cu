@@ -194,7 +194,7 @@ struct Server {
   std::deque<std::unique_ptr<Req>> pending;
   std::map<int64_t, std::unique_ptr<Req>> active, done;
   cudaStream_t s = nullptr;
-  DevBuf cols, packs, nrm, scale, blk_a, blk_b;
+  DevBuf cols, packs, nrm, scale, blk_a, blk_b, hall;
   int64_t steps = 0;
 };
 
@@ -369,11 +369,16 @@ static void arnoldi_step(Server& S) {
   std::vector<std::pair<Req*, int>> who;
   int kmax = 1;
   int64_t nmax = 1;
+  int ncols = 0;
+  for (Req* q : reqs) ncols += q->nrhs;
+  const int ldh0 = S.m + 1;
+  if (S.hall.bytes < sizeof(double2) * (size_t)ncols * ldh0) S.hall.alloc(sizeof(double2) * (size_t)ncols * ldh0 * 2);
   for (Req* q : reqs) {
     const int64_t n = S.ops[q->op]->mesh.nf;
     for (int c = 0; c < q->nrhs; ++c) {
+      // dot products of all columns land in one contiguous buffer: one copy to the host per pass
       cds.push_back(ColDesc{q->V.as<double2>() + (int64_t)c * (S.m + 1) * n, q->w.as<double2>() + (int64_t)c * n,
-                            q->h.as<double2>() + (int64_t)c * (S.m + 1), n, q->k + 1, 0});
+                            S.hall.as<double2>() + (int64_t)cds.size() * ldh0, n, q->k + 1, 0});
       who.push_back({q, c});
     }
     kmax = std::max(kmax, q->k + 1);
@@ -391,9 +396,7 @@ static void arnoldi_step(Server& S) {
   for (int pass = 0; pass < 2; ++pass) {
     k_dots<<<nc * kmax, 256, 0, S.s>>>(S.cols.as<ColDesc>(), nc, kmax);
     k_update<<<nc * chunks, 256, 0, S.s>>>(S.cols.as<ColDesc>(), nc, chunks);
-    for (int i = 0; i < nc; ++i)
-      VIE_CUDA(cudaMemcpyAsync(&hbuf[(size_t)i * ldh], cds[i].h, sizeof(double2) * cds[i].k, cudaMemcpyDeviceToHost,
-                               S.s));
+    VIE_CUDA(cudaMemcpyAsync(hbuf.data(), S.hall.p, sizeof(double2) * (size_t)nc * ldh, cudaMemcpyDeviceToHost, S.s));
     VIE_CUDA(cudaStreamSynchronize(S.s));
     for (int i = 0; i < nc; ++i)
       for (int j = 0; j < cds[i].k; ++j) hsum[i][j] += cd(hbuf[(size_t)i * ldh + j].x, hbuf[(size_t)i * ldh + j].y);

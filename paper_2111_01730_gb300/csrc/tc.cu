@@ -16,14 +16,17 @@
 // bf16 in the canonical no-swizzle K-major core-matrix layout and copied into
 // shared memory with one bulk asynchronous copy (cp.async.bulk, completion on an
 // mbarrier) per k-chunk; the coefficient vectors X are converted to the same
-// layout by the CTA's threads.  Two shared-memory buffers overlap the copies and
-// conversions of chunk k+1 with the MMAs of chunk k.  One thread issues the
-// MMAs; the four warps drain TMEM with tcgen05.ld and write the outputs.
+// layout by the CTA's threads.  Four CTAs per SM (49 KB of shared memory and
+// 128 TMEM columns each) overlap one another's copies, conversions and MMAs.
+// One thread issues the MMAs; eight warps drain TMEM with tcgen05.ld.
 // Blocks too small to fill a tile stay on the SIMT path (stage_kernel).
 //
 // Every wait on an mbarrier is bounded; a CTA that gives up records the event in
 // an error flag that the host reads after the apply.
 #include <cuda_bf16.h>
+
+#include <map>
+#include <tuple>
 
 #include "internal.h"
 
@@ -33,10 +36,11 @@ namespace {
 
 constexpr int kKc = 32;        // complex columns (K) per chunk
 constexpr int kRows = 128;     // right-hand sides per MMA (M of the instruction)
-constexpr int kMaxN = 128;     // output rows per work item (N of the instruction)
-constexpr int kThreads = 128;  // four warps: one TMEM lane quarter each
-constexpr int kTileA = 4 * kRows * kKc * 2;   // bytes: Xr_hi, Xr_lo, Xi_hi, Xi_lo
-constexpr int kTileBMax = 4 * kMaxN * kKc * 2;
+constexpr int kMaxN = 64;      // output rows per work item (N of the instruction)
+constexpr int kTmemCols = 2 * kMaxN;  // D_r and D_i
+constexpr int kThreads = 256;  // eight warps; warp w drains TMEM lane quarter w % 4
+constexpr int kTileA = 4 * kRows * kKc * 2;   // bytes: Xr_hi, Xr_lo, Xi_hi, Xi_lo (32 KB)
+constexpr int kTileBMax = 4 * kMaxN * kKc * 2;  // 16 KB
 constexpr uint32_t kSpinLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,8 +95,15 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
 // ---------------------------------------------------------------------------
 // packing: c64 row-major block rows [m0, m0+Mc) -> bf16 tiles per 32-column chunk
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int seg_of(const TcItem& it, int m) {
+  int sgi = 0;
+  for (int q = 1; q < it.nseg; ++q)
+    if (m >= it.seg[q].start) sgi = q;
+  return sgi;
+}
+
 __global__ void tc_pack_kernel(const TcItem* items, int nitems, const float2* mats, __nv_bfloat16* out) {
-  const TcItem it = items[blockIdx.x];
+  const TcItem& it = items[blockIdx.x];
   const int nk = (it.K + kKc - 1) / kKc;
   const int64_t tile = (int64_t)4 * it.n * kKc;  // bf16 elements per k-chunk tile
   for (int64_t e = threadIdx.x; e < (int64_t)nk * it.n * kKc; e += blockDim.x) {
@@ -101,7 +112,10 @@ __global__ void tc_pack_kernel(const TcItem* items, int nitems, const float2* ma
     const int r = rem / kKc, k = rem % kKc;
     const int kk = kc * kKc + k;
     float2 a = make_float2(0.f, 0.f);
-    if (r < it.mc && kk < it.K) a = mats[it.mat_off + (int64_t)(it.m0 + r) * it.ld + kk];
+    if (r < it.mc && kk < it.K) {
+      const TcSeg& sg = it.seg[seg_of(it, r)];
+      a = mats[sg.mat_off + (int64_t)(sg.row0 + r - sg.start) * sg.ld + kk];
+    }
     __nv_bfloat16 rh, rl, ih, il;
     split_bf16(a.x, rh, rl);
     split_bf16(a.y, ih, il);
@@ -116,89 +130,95 @@ __global__ void tc_pack_kernel(const TcItem* items, int nitems, const float2* ma
 }
 
 // ---------------------------------------------------------------------------
-// the tensor-core stage kernel (persistent over work items)
+// the tensor-core stage kernel (persistent over work items; several CTAs per SM
+// interleave their copy / convert / MMA phases)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(const TcItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(kThreads, 4) tc_stage_kernel(const TcItem* __restrict__ items, int nitems,
                                                                 const uint8_t* __restrict__ btiles,
                                                                 const float2* xt, float2* yt, float2* coef,
                                                                 int nrhs, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA[2] = {smem, smem + kTileA};
-  uint8_t* sB[2] = {smem + 2 * kTileA, smem + 2 * kTileA + kTileBMax};
-  __shared__ __align__(8) uint64_t load_bar[2], mma_bar[2];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kTileA;
+  __shared__ __align__(8) uint64_t load_bar, mma_bar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&load_bar[b])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mma_bar[b])));
-    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&load_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mma_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;  // D_r: columns [0, 128), D_i: [128, 256)
-  uint32_t load_phase[2] = {0, 0}, mma_phase[2] = {0, 0};
+  const uint32_t tmem = tmem_base;  // D_r: columns [0, kMaxN), D_i: [kMaxN, 2 kMaxN)
+  uint32_t load_phase = 0, mma_phase = 0;
   bool ok = true;
   const int nrc = (nrhs + kRows - 1) / kRows;
   for (int w = blockIdx.x; w < nitems * nrc && ok; w += gridDim.x) {
-    const TcItem it = items[w / nrc];
+    const TcItem& it = items[w / nrc];
     const int r0 = (w % nrc) * kRows;
     const int nk = (it.K + kKc - 1) / kKc;
     const float2* x = (it.in_space == SP_X ? xt : (it.in_space == SP_Y ? (const float2*)yt : coef)) +
                       (int64_t)it.in_off * nrhs;
     const uint32_t tile_bytes = 4u * it.n * kKc * 2u;
-    const uint32_t id_n = (uint32_t)it.n;
-    int pending[2] = {0, 0};
     for (int kc = 0; kc < nk && ok; ++kc) {
-      const int b = kc & 1;
-      if (pending[b]) {  // the MMAs that read this buffer two chunks ago must be done
-        ok = mbar_wait(smem_u32(&mma_bar[b]), mma_phase[b]);
-        mma_phase[b] ^= 1;
-        pending[b] = 0;
+      if (kc > 0) {  // single buffer: the previous chunk's MMAs must have read it
+        ok = mbar_wait(smem_u32(&mma_bar), mma_phase);
+        mma_phase ^= 1;
       }
       if (tid == 0 && ok) {
-        const uint32_t bar = smem_u32(&load_bar[b]);
+        const uint32_t bar = smem_u32(&load_bar);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(tile_bytes) : "memory");
         const uint8_t* src = btiles + it.b_off + (int64_t)kc * tile_bytes;
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(smem_u32(sB[b])), "l"(src), "r"(tile_bytes), "r"(bar) : "memory");
+                     :: "r"(smem_u32(sB)), "l"(src), "r"(tile_bytes), "r"(bar) : "memory");
       }
-      // X chunk -> bf16 hi/lo tiles (rows = right-hand sides, columns = k)
-      __nv_bfloat16* a = reinterpret_cast<__nv_bfloat16*>(sA[b]);
+      // X chunk -> bf16 hi/lo tiles (rows = right-hand sides, columns = k).  All global
+      // loads of a thread are issued before its shared-memory stores, so they overlap.
+      __nv_bfloat16* a = reinterpret_cast<__nv_bfloat16*>(sA);
       constexpr int part = kRows * kKc;
-      for (int e = tid; e < kRows * kKc; e += kThreads) {
+      constexpr int per = kRows * kKc / kThreads;  // 16 elements per thread
+      const int kvalid = min(kKc, it.K - kc * kKc);
+      float2 v[per];
+#pragma unroll
+      for (int u = 0; u < per; ++u) {
+        const int e = tid + u * kThreads;
         const int k = e / kRows, r = e % kRows;  // consecutive threads: consecutive rhs
-        const int kk = kc * kKc + k, rr = r0 + r;
-        float2 v = make_float2(0.f, 0.f);
-        if (kk < it.K && rr < nrhs) v = x[(int64_t)kk * nrhs + rr];
+        const int rr = r0 + r;
+        v[u] = (k < kvalid && rr < nrhs) ? __ldg(x + (int64_t)(kc * kKc + k) * nrhs + rr) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < per; ++u) {
+        const int e = tid + u * kThreads;
+        const int k = e / kRows, r = e % kRows;
         __nv_bfloat16 h, l;
         const int ci = cm_index(r, k);
-        split_bf16(v.x, h, l);
+        split_bf16(v[u].x, h, l);
         a[ci] = h;
         a[part + ci] = l;
-        split_bf16(v.y, h, l);
+        split_bf16(v[u].y, h, l);
         a[2 * part + ci] = h;
         a[3 * part + ci] = l;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0 && ok) {
-        ok = mbar_wait(smem_u32(&load_bar[b]), load_phase[b]);
-        load_phase[b] ^= 1;
+        ok = mbar_wait(smem_u32(&load_bar), load_phase);
+        load_phase ^= 1;
         if (ok) {
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t A0 = smem_u32(sA[b]), B0 = smem_u32(sB[b]);
-          const uint32_t pa = (uint32_t)part * 2u, pb = id_n * kKc * 2u;  // bytes per hi/lo part
+          const uint32_t A0 = smem_u32(sA), B0 = smem_u32(sB);
+          const uint32_t pa = (uint32_t)part * 2u, pb = (uint32_t)it.n * kKc * 2u;  // bytes per hi/lo plane
           const uint32_t Xrh = A0, Xrl = A0 + pa, Xih = A0 + 2 * pa, Xil = A0 + 3 * pa;
           const uint32_t Arh = B0, Arl = B0 + pb, Aih = B0 + 2 * pb, Ail = B0 + 3 * pb;
           const uint32_t idp = instr_desc(it.n, 0), idm = instr_desc(it.n, 1);
-          const uint32_t Dr = tmem, Di = tmem + 128;
+          const uint32_t Dr = tmem, Di = tmem + kMaxN;
           for (int ks = 0; ks < kKc / 16; ++ks) {
             const uint32_t o = ks * 256;  // two core matrices along K
             const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
@@ -217,50 +237,52 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(const TcItem* __r
             mma_bf16(Di, smem_desc(Xil + o), smem_desc(Arh + o), idp, 1);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                       :: "r"(smem_u32(&mma_bar[b])) : "memory");
+                       :: "r"(smem_u32(&mma_bar)) : "memory");
         }
       }
-      // every thread tracks the commit of this buffer
-      pending[b] = 1;
-      __syncthreads();
       ok = __syncthreads_and(ok ? 1 : 0) != 0;
     }
-    // drain: wait for the outstanding commits (the last one covers all MMAs issued before it)
-    for (int b = 0; b < 2 && ok; ++b)
-      if (pending[b]) {
-        ok = mbar_wait(smem_u32(&mma_bar[b]), mma_phase[b]);
-        mma_phase[b] ^= 1;
-        pending[b] = 0;
-      }
+    if (ok) {  // the last commit covers every MMA of the item
+      ok = mbar_wait(smem_u32(&mma_bar), mma_phase);
+      mma_phase ^= 1;
+    }
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: warp w owns TMEM lanes (right-hand sides) 32w .. 32w+31
-    float2* y = (it.out_space == SP_Y ? yt : coef) + (int64_t)it.out_off * nrhs;
-    const int rr = r0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < it.n; c0 += 8) {
+    // epilogue: warp w drains TMEM lanes (right-hand sides) 32 (w % 4) .. +31,
+    // warps 0-3 the first half of the output rows, warps 4-7 the second half
+    const int rr = r0 + (warp & 3) * 32 + lane;
+    const int half = it.n / 2;
+    const int cbeg = (warp >> 2) * half;
+    for (int c0 = cbeg; c0 < cbeg + half; c0 += 8) {
       uint32_t vr[8], vi[8];
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+      const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + c0;
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                    : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7])
                    : "r"(lane_addr));
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                    : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7])
-                   : "r"(lane_addr + 128));
+                   : "r"(lane_addr + kMaxN));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (rr < nrhs) {
+        float2 old[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {  // all reads in flight before the writes
+          const int m = c0 + j;
+          old[j] = make_float2(0.f, 0.f);
+          if (m < it.mc) {
+            const TcSeg& sg = it.seg[seg_of(it, m)];
+            if (sg.accumulate)
+              old[j] = ((sg.out_space == SP_Y ? yt : coef) + (sg.out_off + sg.row0 + m - sg.start) * nrhs)[rr];
+          }
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int m = c0 + j;
           if (m < it.mc) {
-            float2* dst = y + (int64_t)(it.m0 + m) * nrhs + rr;
-            const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
-            if (it.accumulate) {
-              float2 o = *dst;
-              *dst = make_float2(o.x + re, o.y + im);
-            } else {
-              *dst = make_float2(re, im);
-            }
+            const TcSeg& sg = it.seg[seg_of(it, m)];
+            ((sg.out_space == SP_Y ? yt : coef) + (sg.out_off + sg.row0 + m - sg.start) * nrhs)[rr] =
+                make_float2(old[j].x + __uint_as_float(vr[j]), old[j].y + __uint_as_float(vi[j]));
           }
         }
       }
@@ -271,40 +293,53 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(const TcItem* __r
   if (!ok && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t tc_smem_bytes() { return 2 * (size_t)kTileA + 2 * (size_t)kTileBMax + 1024; }
+size_t tc_smem_bytes() { return (size_t)kTileA + (size_t)kTileBMax + 1024; }
 
 bool tc_eligible(const OpDesc& o) { return o.M >= 16 && o.K >= 32; }
 
 void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s) {
-  // split eligible ops into 128-row work items and pack their bf16 tiles
+  // Eligible blocks that read the same input slice (the V0 blocks and the leaf block
+  // of one leaf; the two W blocks of the children of one node) share work items of
+  // up to 64 rows, so each input chunk is converted once for all of them.
+  std::map<std::tuple<int, int64_t, int>, std::vector<size_t>> groups;
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (tc_eligible(ops[i])) groups[{ops[i].in_space, ops[i].in_off, ops[i].K}].push_back(i);
   std::vector<TcItem> items;
   int64_t off = 0;
-  for (size_t i = 0; i < ops.size(); ++i) {
-    const OpDesc& o = ops[i];
-    if (!tc_eligible(o)) continue;
-    for (int m0 = 0; m0 < o.M; m0 += kMaxN) {
-      TcItem t{};
-      t.mat_off = o.mat_off;
-      t.ld = o.ld;
-      t.K = o.K;
-      t.m0 = m0;
-      t.mc = std::min(kMaxN, o.M - m0);
+  for (auto& kv : groups) {
+    TcItem t{};
+    auto flush = [&]() {
+      if (t.mc == 0) return;
       t.n = (t.mc + 15) / 16 * 16;
-      t.in_off = o.in_off;
-      t.out_off = o.out_off;
-      t.in_space = o.in_space;
-      t.out_space = o.out_space;
-      t.accumulate = o.accumulate;
       t.b_off = off;
-      off += (int64_t)((o.K + kKc - 1) / kKc) * 4 * t.n * kKc * 2;
+      off += (int64_t)((t.K + kKc - 1) / kKc) * 4 * t.n * kKc * 2;
       items.push_back(t);
+      TcItem z{};
+      z.in_space = t.in_space; z.in_off = t.in_off; z.K = t.K;
+      t = z;
+    };
+    t.in_space = (int16_t)std::get<0>(kv.first);
+    t.in_off = std::get<1>(kv.first);
+    t.K = std::get<2>(kv.first);
+    for (size_t i : kv.second) {
+      const OpDesc& o = ops[i];
+      for (int r = 0; r < o.M;) {
+        if (t.mc == kMaxN || t.nseg == kTcMaxSeg) flush();
+        const int take = std::min(o.M - r, kMaxN - t.mc);
+        TcSeg& sg = t.seg[t.nseg++];
+        sg.mat_off = o.mat_off; sg.out_off = o.out_off; sg.ld = o.ld; sg.row0 = r; sg.rows = take;
+        sg.start = t.mc; sg.out_space = o.out_space; sg.accumulate = (int16_t)o.accumulate;
+        t.mc += take;
+        r += take;
+      }
     }
+    flush();
   }
   st.tc_items = (int64_t)items.size();
   st.tc_bytes = off;
@@ -341,7 +376,7 @@ void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, 
   }
   const int nrc = (nrhs + kRows - 1) / kRows;
   const int64_t work = st.tc_items * nrc;
-  const int grid = (int)std::min<int64_t>(work, 152);
+  const int grid = (int)std::min<int64_t>(work, 152 * 4);  // four CTAs per SM (smem 49 KB, TMEM 128 columns each)
   tc_stage_kernel<<<grid, kThreads, tc_smem_bytes(), s>>>(st.tc_ops.as<TcItem>(), (int)st.tc_items,
                                                           st.tc_tiles.as<uint8_t>(), (const float2*)xt, (float2*)yt,
                                                           (float2*)coef, nrhs, d_err);

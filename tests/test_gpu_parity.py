@@ -91,3 +91,13 @@ def test_apply_is_deterministic(case):
     a = op.apply(X).clone()
     b = op.apply(X).clone()
     assert torch.equal(a, b)
+
+
+def test_autotune_keeps_results(case):
+    op = pkg.Operator(case["body"], W.K0, tol_con=1e-4, leaf=32)
+    X = torch.from_numpy(W.random_block(case["n"], 1, seed=19)[:, 0]).to(torch.complex64).cuda()
+    before = op.apply(X).clone()
+    choice = op.autotune()
+    assert len(choice) == op.get_stats().apply_stages_z and np.all((choice >= 0) & (choice < 9))
+    after = op.apply(X)
+    assert (torch.linalg.norm(after - before) / torch.linalg.norm(before)).item() < 1e-6
