@@ -218,6 +218,12 @@ vie_status vie_stats(const vie_op* op, vie_stats_t* out);
  * apply packs the factor tiles (device memory about the size of the factors). */
 vie_status vie_check(vie_op* op, void* stream);
 
+/* Failure-path self-test of the bounded device waits used by the tensor-core
+ * kernels: a kernel waits `spins` (1 .. 2^20) polls on an mbarrier that nothing
+ * arrives on and gives up; returns VIE_ETIMEOUT (the expected outcome), with the
+ * context still usable.  VIE_EINVAL for spins out of range. */
+vie_status vie_wait_selftest(int32_t spins, void* stream);
+
 /* ---- serving: continuous batching of solves against resident operators ----
  * (spec serving loop; the paper's solver phase is Eq. 6 with Zinv.)
  * A server holds up to `nops` built operators (not owned).  Requests are

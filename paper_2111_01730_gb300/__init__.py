@@ -24,7 +24,7 @@ VIE_C64, VIE_C128 = 0, 1
 
 # every symbol declared in include/vie.h
 EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
-           "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_destroy", "vie_last_error",
+           "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_wait_selftest", "vie_destroy", "vie_last_error",
            "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy"]
 
 
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "vie_tree_perm": [P, P],
         "vie_stats": [P, P],
         "vie_check": [P, P],
+        "vie_wait_selftest": [I32, P],
         "vie_server_create": [P, I32, I32, I32, I64, P, P],
         "vie_server_submit": [P, I32, P, I64, D, P],
         "vie_server_step": [P, P, P],

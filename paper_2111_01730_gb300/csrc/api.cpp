@@ -320,6 +320,20 @@ vie_status vie_check(vie_op* h, void* stream) {
   });
 }
 
+vie_status vie_wait_selftest(int32_t spins, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(spins >= 1 && spins <= (1 << 20), VIE_EINVAL, "spins out of range [1, 2^20]");
+    DevBuf st;
+    st.alloc(sizeof(int));
+    VIE_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), (cudaStream_t)stream));
+    wait_timeout_check((uint32_t)spins, st.as<int>(), (cudaStream_t)stream);
+    int h = 0;
+    VIE_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    VIE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h) throw Error{VIE_ETIMEOUT, "bounded device wait ran out (expected in this self-test)"};
+  });
+}
+
 vie_status vie_stats(const vie_op* h, vie_stats_t* out) {
   return guarded([&] {
     VIE_REQUIRE(h && out, VIE_EINVAL, "null argument");

@@ -24,9 +24,6 @@ template <class T> struct C2;
 template <> struct C2<float> { using type = float2; };
 template <> struct C2<double> { using type = double2; };
 
-template <class TV>
-__device__ __forceinline__ typename C2<TV>::type ldv(const typename C2<TV>::type* p) { return __ldg(p); }
-
 // Accumulate row . x for a row of K entries starting at A (row-major), lanes li..g.
 template <class TM, class TV, int NR>
 __device__ __forceinline__ void row_dot(const typename C2<TM>::type* __restrict__ A, int K, int li, int g,
@@ -400,9 +397,20 @@ static void run_stages(const Program& p, int64_t nrhs, void* xt, void* yt, void*
 void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
                          int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s) {
   const bool tc = p.tc_ready && dtype == VIE_C64 && p.factor_dtype == VIE_C64 && nrhs >= kTcMinRhs;
-  if (!p.graph || p.g_nrhs != nrhs || p.g_dtype != dtype || p.g_xt != d_xt || p.g_yt != d_yt || p.g_coef != d_c ||
-      p.g_tc != tc) {
-    if (p.graph) { cudaGraphExecDestroy(p.graph); p.graph = nullptr; }
+  Program::GraphEntry* hit = nullptr;
+  for (auto& g : p.graphs)
+    if (g.exec && g.nrhs == nrhs && g.dtype == dtype && g.tc == tc && g.xt == d_xt && g.yt == d_yt && g.coef == d_c)
+      hit = &g;
+  if (!hit) {
+    if (p.graphs.size() < kGraphCache) {
+      p.graphs.emplace_back();
+      hit = &p.graphs.back();
+    } else {
+      hit = &p.graphs[0];
+      for (auto& g : p.graphs)
+        if (g.used < hit->used) hit = &g;
+      if (hit->exec) { cudaGraphExecDestroy(hit->exec); hit->exec = nullptr; }
+    }
     if (!p.capture_stream) VIE_CUDA(cudaStreamCreateWithFlags(&p.capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     VIE_CUDA(cudaStreamBeginCapture(p.capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -416,13 +424,14 @@ void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void*
       throw;
     }
     VIE_CUDA(cudaStreamEndCapture(p.capture_stream, &g));
-    cudaError_t ie = cudaGraphInstantiate(&p.graph, g, 0);
+    cudaError_t ie = cudaGraphInstantiate(&hit->exec, g, 0);
     cudaGraphDestroy(g);
     VIE_CUDA(ie);
-    p.g_nrhs = nrhs; p.g_dtype = dtype; p.g_xt = d_xt; p.g_yt = d_yt; p.g_coef = d_c; p.g_tc = tc;
+    hit->nrhs = nrhs; hit->dtype = dtype; hit->tc = tc; hit->xt = d_xt; hit->yt = d_yt; hit->coef = d_c;
   }
-  if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, p.graph);
-  else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, p.graph);
+  hit->used = ++p.graph_clock;
+  if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, hit->exec);
+  else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, hit->exec);
 }
 
 void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
@@ -478,7 +487,8 @@ int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s,
   VIE_CUDA(cudaStreamSynchronize(s));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (p.graph) { cudaGraphExecDestroy(p.graph); p.graph = nullptr; }  // tiles changed
+  for (auto& g : p.graphs)  // tiles changed
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
   return nst;
 }
 

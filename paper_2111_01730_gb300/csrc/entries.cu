@@ -476,14 +476,12 @@ __global__ void rhs_kernel(EntryCtx c, int64_t n, const double* khat, const doub
       const TetDev t = c.tets[T[s]];
       const double h = c.h, vol = h * h * h / 6.0;
       const double ca = (s == 0 ? 1.0 : -1.0) * c_area[t.type][A[s]] * h * h / (3.0 * vol);
-      V3 o = v3(t.vx * h, t.vy * h, t.vz * h);
       Elem E{t.type, -1, 0, 0, 0};
       V3 qa = kuhn_vertex(t.type, A[s], 0, 0, 0, h);
       for (int i = 0; i < 27; ++i) {
         double w;
         V3 rl = rule_point(E, 3, i, h, w);
-        V3 r = v3(double(t.vx + 0) * h, double(t.vy) * h, double(t.vz) * h) + rl;
-        (void)o;
+        V3 r = v3(double(t.vx) * h, double(t.vy) * h, double(t.vz) * h) + rl;
         double sn, cs;
         sincos(-c.k0 * dot(kh, r), &sn, &cs);
         double f = w * ca * dot(rl - qa, pl);

@@ -138,8 +138,6 @@ void entries_pairs(const Geometry& g, const int32_t* rows, const int32_t* cols, 
                    double2* out, cudaStream_t s, bool far32 = false);
 void rhs_planewave(const Geometry& g, const double* khat, const double* pol, int nrhs, double2* V,
                    cudaStream_t s);
-void farfield(const Geometry& g, const double2* I, int nrhs, const double* dirs, int ndir,
-              double* rcs, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // batched interpolative decomposition (id.cu), Eq. (7)
@@ -208,19 +206,26 @@ struct Program {         // one operator's apply: gather, stages, scatter
   int64_t entries = 0, bytes = 0;
   bool tc_ready = false;
   DevBuf err;            // device int: a bounded wait in a tensor-core kernel ran out
-  // CUDA graph of the stage launches (the gather and scatter stay outside: they
-  // touch the caller's X and Y); rebuilt when nrhs, dtype or workspaces change
-  cudaGraphExec_t graph = nullptr;
+  // CUDA graphs of the stage launches (the gather and scatter stay outside: they
+  // touch the caller's X and Y), one per (nrhs, dtype, path, workspaces), least
+  // recently used evicted beyond kGraphCache
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t nrhs = -1;
+    int dtype = -1;
+    bool tc = false;
+    const void *xt = nullptr, *yt = nullptr, *coef = nullptr;
+    uint64_t used = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
   cudaStream_t capture_stream = nullptr;
-  int64_t g_nrhs = -1;
-  int g_dtype = -1;
-  const void *g_xt = nullptr, *g_yt = nullptr, *g_coef = nullptr;
-  bool g_tc = false;
   Program() = default;
   Program(const Program&) = delete;
   Program& operator=(const Program&) = delete;
   ~Program() {
-    if (graph) cudaGraphExecDestroy(graph);
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
     if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
@@ -230,7 +235,9 @@ bool tc_eligible(const OpDesc& o);
 void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s);
 void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* d_err, cudaStream_t s);
 size_t tc_smem_bytes();
+void wait_timeout_check(uint32_t spins, int* d_status, cudaStream_t s);
 constexpr int kTcMinRhs = 16;
+constexpr size_t kGraphCache = 8;
 constexpr int64_t kDenseInverseLimit = 32768;  // largest diagonal block formed densely by the inverse builder   // the tensor-core path serves nrhs >= 16 (c64 factors and vectors)
 
 void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles);

@@ -179,32 +179,41 @@ __global__ void __launch_bounds__(kThreads, 4) tc_stage_kernel(const TcItem* __r
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      :: "r"(smem_u32(sB)), "l"(src), "r"(tile_bytes), "r"(bar) : "memory");
       }
-      // X chunk -> bf16 hi/lo tiles (rows = right-hand sides, columns = k).  All global
-      // loads of a thread are issued before its shared-memory stores, so they overlap.
-      __nv_bfloat16* a = reinterpret_cast<__nv_bfloat16*>(sA);
-      constexpr int part = kRows * kKc;
-      constexpr int per = kRows * kKc / kThreads;  // 16 elements per thread
+      // X chunk -> bf16 hi/lo tiles (rows = right-hand sides, columns = k).  A thread
+      // owns (rhs r, 8 consecutive k): it issues its 8 global loads first, then writes
+      // one 16-byte row segment of a core matrix per plane (bank-conflict free).
+      constexpr int part = kRows * kKc;  // bf16 elements per plane
+      constexpr int groups = kRows * (kKc / 8);  // (rhs, k-group) pairs per chunk
       const int kvalid = min(kKc, it.K - kc * kKc);
-      float2 v[per];
 #pragma unroll
-      for (int u = 0; u < per; ++u) {
-        const int e = tid + u * kThreads;
-        const int k = e / kRows, r = e % kRows;  // consecutive threads: consecutive rhs
+      for (int gi = tid; gi < groups; gi += kThreads) {
+        const int r = gi % kRows, kg = gi / kRows;  // consecutive threads: consecutive rhs
         const int rr = r0 + r;
-        v[u] = (k < kvalid && rr < nrhs) ? __ldg(x + (int64_t)(kc * kKc + k) * nrhs + rr) : make_float2(0.f, 0.f);
-      }
+        float2 v[8];
 #pragma unroll
-      for (int u = 0; u < per; ++u) {
-        const int e = tid + u * kThreads;
-        const int k = e / kRows, r = e % kRows;
-        __nv_bfloat16 h, l;
-        const int ci = cm_index(r, k);
-        split_bf16(v[u].x, h, l);
-        a[ci] = h;
-        a[part + ci] = l;
-        split_bf16(v[u].y, h, l);
-        a[2 * part + ci] = h;
-        a[3 * part + ci] = l;
+        for (int j = 0; j < 8; ++j) {
+          const int k = kg * 8 + j;
+          v[j] = (k < kvalid && rr < nrhs) ? __ldg(x + (int64_t)(kc * kKc + k) * nrhs + rr) : make_float2(0.f, 0.f);
+        }
+        uint32_t rh[4], rl[4], ih[4], il[4];  // bf16 pairs
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          __nv_bfloat16 h0, l0, h1, l1;
+          split_bf16(v[j].x, h0, l0);
+          split_bf16(v[j + 1].x, h1, l1);
+          rh[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          rl[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          split_bf16(v[j].y, h0, l0);
+          split_bf16(v[j + 1].y, h1, l1);
+          ih[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          il[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        const int ci = cm_index(r, kg * 8);  // start of the 16-byte row segment
+        uint4* a4 = reinterpret_cast<uint4*>(sA);
+        a4[ci / 8] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+        a4[(part + ci) / 8] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+        a4[(2 * part + ci) / 8] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+        a4[(3 * part + ci) / 8] = make_uint4(il[0], il[1], il[2], il[3]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -294,6 +303,29 @@ __global__ void __launch_bounds__(kThreads, 4) tc_stage_kernel(const TcItem* __r
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
+}
+
+// ---------------------------------------------------------------------------
+// failure-path check of the bounded mbarrier wait: wait on a barrier that
+// nothing arrives on, with a short spin limit, and report the timeout
+// ---------------------------------------------------------------------------
+__global__ void wait_timeout_kernel(uint32_t spins, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < spins && !done; ++it)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(smem_u32(&bar)), "r"(0) : "memory");
+  if (threadIdx.x == 0) *status = done ? 0 : 1;
+}
+
+void wait_timeout_check(uint32_t spins, int* d_status, cudaStream_t s) {
+  wait_timeout_kernel<<<1, 32, 0, s>>>(spins, d_status);
+  VIE_CUDA(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
