@@ -297,6 +297,32 @@ def run_serving(args):
     return 0
 
 
+def zinv_timing(op, pkg, x, y, steps, torch):
+    """Zinv apply (Algorithm 1 levels present in the operator) and one preconditioned MVP (Z + Zinv)."""
+    st = op.get_stats()
+    ez = int(op.program_info(pkg.VIE_OP_ZINV)[0].sum())
+    t = torch.empty_like(y)
+    for _ in range(3):
+        op.apply(x, y, op=pkg.VIE_OP_ZINV)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(steps):
+        op.apply(x, y, op=pkg.VIE_OP_ZINV)
+    e[1].record(stream)
+    for _ in range(steps):
+        op.apply(x, t, op=pkg.VIE_OP_ZINV)
+        op.apply(t, y)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / steps
+    return {"ms_per_apply": round(ms, 4), "gbs": round((8 * ez + 16 * op.n * x.numel() // op.n) / (ms * 1e-3) / 1e9, 1),
+            "factor_entries": ez, "stages": int(st.apply_stages_zinv), "top_level": int(st.zinv_top_level),
+            "invert_seconds": round(st.invert_seconds, 2),
+            "mvp_with_precond_ms": round(e[1].elapsed_time(e[2]) / steps, 4)}
+
+
 def nrhs_for_tune(args):
     """The stage-tiling autotuner serves the single-RHS kernel."""
     return args.nrhs == 1 and not args.no_autotune
@@ -329,6 +355,7 @@ def main():
                     help="right-hand sides per apply (>= 16 runs the tensor-core path)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default stage tiling")
+    ap.add_argument("--zinv", action="store_true", help="also build Zinv (chi_fact 1e-1) and time its apply")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (solves/s, p50/p99 latency)")
     ap.add_argument("--requests", type=int, default=120)
     ap.add_argument("--rate", type=float, default=100.0, help="Poisson arrival rate (requests/s) for --serve")
@@ -355,7 +382,8 @@ def main():
     hbm, peak_kind = peaks()
     body, desc = workload(args.radius)
     t0 = time.perf_counter()
-    op = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c64", seed=1)
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=(1e-1 if args.zinv else 0.0), leaf=64,
+                      factor_dtype="c64", seed=1)
     build_s = time.perf_counter() - t0
     tune = op.autotune(pkg.VIE_OP_Z) if nrhs_for_tune(args) else None
     st = op.get_stats()
@@ -449,6 +477,8 @@ def main():
             "gpu_launches": launches_per_apply * args.steps,
             "clocks": clk,
         }
+        if args.zinv:
+            line["zinv"] = zinv_timing(op, pkg, x, y, args.steps, torch)
         line["roofline"].update({"peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms],
                                  "stage_gbs": [round(8 * float(e) / (float(t) * 1e6), 1)
                                                for e, t in zip(entries, stage_ms)]})

@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(kThreads, 4) tc_stage_kernel(const TcItem* __r
   uint8_t* sB = smem + kTileA;
   __shared__ __align__(8) uint64_t load_bar, mma_bar;
   __shared__ uint32_t tmem_base;
+  __shared__ float2* s_dst[kMaxN];   // output row base (row m of the item, right-hand side 0)
+  __shared__ int s_acc[kMaxN];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&load_bar)));
@@ -167,6 +169,11 @@ __global__ void __launch_bounds__(kThreads, 4) tc_stage_kernel(const TcItem* __r
     const float2* x = (it.in_space == SP_X ? xt : (it.in_space == SP_Y ? (const float2*)yt : coef)) +
                       (int64_t)it.in_off * nrhs;
     const uint32_t tile_bytes = 4u * it.n * kKc * 2u;
+    if (tid < it.mc) {  // output row pointers of the item, resolved once
+      const TcSeg& sg = it.seg[seg_of(it, tid)];
+      s_dst[tid] = (sg.out_space == SP_Y ? yt : coef) + (sg.out_off + sg.row0 + tid - sg.start) * nrhs;
+      s_acc[tid] = sg.accumulate;
+    }
     for (int kc = 0; kc < nk && ok; ++kc) {
       if (kc > 0) {  // single buffer: the previous chunk's MMAs must have read it
         ok = mbar_wait(smem_u32(&mma_bar), mma_phase);
@@ -278,21 +285,12 @@ __global__ void __launch_bounds__(kThreads, 4) tc_stage_kernel(const TcItem* __r
 #pragma unroll
         for (int j = 0; j < 8; ++j) {  // all reads in flight before the writes
           const int m = c0 + j;
-          old[j] = make_float2(0.f, 0.f);
-          if (m < it.mc) {
-            const TcSeg& sg = it.seg[seg_of(it, m)];
-            if (sg.accumulate)
-              old[j] = ((sg.out_space == SP_Y ? yt : coef) + (sg.out_off + sg.row0 + m - sg.start) * nrhs)[rr];
-          }
+          old[j] = (m < it.mc && s_acc[m]) ? s_dst[m][rr] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int m = c0 + j;
-          if (m < it.mc) {
-            const TcSeg& sg = it.seg[seg_of(it, m)];
-            ((sg.out_space == SP_Y ? yt : coef) + (sg.out_off + sg.row0 + m - sg.start) * nrhs)[rr] =
-                make_float2(old[j].x + __uint_as_float(vr[j]), old[j].y + __uint_as_float(vi[j]));
-          }
+          if (m < it.mc) s_dst[m][rr] = make_float2(old[j].x + __uint_as_float(vr[j]), old[j].y + __uint_as_float(vi[j]));
         }
       }
     }
