@@ -363,11 +363,18 @@ def zblock(E: Elements, rows, cols, chunk: int = 256) -> np.ndarray:
     return Z
 
 
-def rhs_planewave(E: Elements, khat, pol) -> np.ndarray:
-    """V(m) = int f_m . pol exp(-j k0 khat . r) dv (Eq. 5), tet_conical(3); (N, nrhs)."""
+def rhs_planewave(E: Elements, khat, pol, rows=None) -> np.ndarray:
+    """V(m) = int f_m . pol exp(-j k0 khat . r) dv (Eq. 5), tet_conical(3); (N, nrhs).
+
+    With `rows` (face ids), only those entries are formed, from the tets that
+    touch them: (len(rows), nrhs)."""
     mesh = E.mesh
-    nt = len(mesh["tets"])
-    t = np.arange(nt)
+    if rows is None:
+        t = np.arange(len(mesh["tets"]))
+    else:
+        rows = np.asarray(rows, dtype=np.int64)
+        t = np.unique(np.concatenate([mesh["face_tp"][rows], mesh["face_tm"][rows]]))
+        t = t[t >= 0]
     r, w = E.tet_rule(t, Q.tet_conical(3))
     f = swg_eval(E.geo, t, r)  # (nt, q, 4, 3)
     khat = np.atleast_2d(khat)
@@ -376,5 +383,5 @@ def rhs_planewave(E: Elements, khat, pol) -> np.ndarray:
     for j in range(len(khat)):
         ph = np.exp(-1j * E.k0 * (r @ khat[j]))  # (nt, q)
         val = np.einsum("tq,tqad,d->ta", w * ph, f, pol[j])
-        np.add.at(V[:, j], mesh["tet_faces"].ravel(), val.ravel())
-    return V
+        np.add.at(V[:, j], mesh["tet_faces"][t].ravel(), val.ravel())
+    return V if rows is None else V[rows]

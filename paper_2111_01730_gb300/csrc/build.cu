@@ -13,7 +13,7 @@
 //
 // Row sampling (the paper does not say how rows are chosen for the IDs): for
 // a candidate column set J of size c, the c + 4 rows of tau nearest to the
-// bounding box of nu plus c/2 + oversample rows drawn uniformly at random
+// bounding box of nu plus c + oversample rows drawn uniformly at random
 // without replacement (seeded); all rows when tau has no more than that.  The
 // near rows carry the strong near-field couplings that set the rank of
 // touching blocks; uniform rows alone miss them.
@@ -96,7 +96,7 @@ struct Sampler {
   void rows(int lev, int64_t idx, int nlev, int64_t nidx, int ncand, uint64_t key, std::vector<int32_t>& out) const {
     const int64_t a = t.bounds[lev][idx], b = t.bounds[lev][idx + 1];
     const int64_t sz = b - a;
-    const int nnear = ncand + 4, nrand = ncand / 2 + oversample;
+    const int nnear = ncand + 4, nrand = ncand + oversample;
     out.clear();
     if (sz <= nnear + nrand) {
       for (int64_t p = a; p < b; ++p) out.push_back((int32_t)p);

@@ -123,3 +123,12 @@ def test_energy_balance_lossy_sphere(lossy_sphere):
     e = d / mesh["eps"][:, None, None]
     sig_abs = W.K0 * (np.abs(mesh["eps"].imag)[:, None] * w * (np.abs(e) ** 2).sum(-1)).sum()
     assert abs(sig_ext - (sig_sca + sig_abs)) < 2e-3 * sig_ext
+
+
+def test_rhs_rows_subset_matches_full_vector():
+    body = W.sphere(0.15, 4.0, 1 / 16)
+    E = Elements(build_mesh(body), W.K0)
+    k, p = W.planewave_x_along_z()
+    full = rhs_planewave(E, k, p)
+    rows = np.random.default_rng(3).choice(full.shape[0], size=17, replace=False)
+    assert np.array_equal(rhs_planewave(E, k, p, rows=rows), full[rows])
