@@ -1,4 +1,4 @@
-"""Mie series for homogeneous and coated spheres (oracle; test infrastructure only).
+"""Mie series for homogeneous, coated and multilayer spheres (oracle; test infrastructure only).
 
 The paper validates its RCS against the exact Mie series (Sec. IV-A); the
 series is textbook theory (Bohren & Huffman, ch. 4 and Sec. 8.1), written here
@@ -89,6 +89,49 @@ def coefficients_coated(x: float, y: float, m1: complex, m2: complex, nmax: int 
     return a, b
 
 
+def coefficients_multilayer(xs, ms, nmax: int | None = None):
+    """a_n, b_n of a sphere of concentric layers.
+
+    Layer j (0 = innermost) has relative index ms[j] and outer size parameter
+    xs[j] (increasing).  Inside layer j the radial function of each mode is
+    f(rho) = psi_n(rho) - A chi_n(rho), rho = ms[j] k r; the innermost is psi_n.
+    At an interface the tangential fields are continuous, which for the
+    logarithmic derivative D = f'/f gives D / m continuous for the electric (a)
+    modes and m D continuous for the magnetic (b) modes; each layer's A follows
+    from D at its inner radius, and D at its outer radius from A.  At the
+    surface (size parameter y = xs[-1], index m = ms[-1]):
+      a_n = (D_a/m psi_n(y) - psi_n'(y)) / (D_a/m xi_n(y) - xi_n'(y)),
+      b_n = (m D_b psi_n(y) - psi_n'(y)) / (m D_b xi_n(y) - xi_n'(y)).
+    """
+    xs = np.asarray(xs, dtype=np.float64)
+    ms = np.asarray(ms, dtype=np.complex128)
+    y = float(xs[-1])
+    if nmax is None:
+        nmax = int(round(y + 4.0 * y ** (1.0 / 3.0) + 2.0))
+    n = np.arange(1, nmax + 1)
+    z0 = ms[0] * xs[0]
+    Da = _dpsi(n, z0) / _psi(n, z0)
+    Db = Da.copy()
+    for j in range(1, len(xs)):
+        Da = Da * ms[j] / ms[j - 1]
+        Db = Db * ms[j - 1] / ms[j]
+        r1, r2 = ms[j] * xs[j - 1], ms[j] * xs[j]
+        p1, dp1, c1, dc1 = _psi(n, r1), _dpsi(n, r1), _chi(n, r1), _dchi(n, r1)
+        p2, dp2, c2, dc2 = _psi(n, r2), _dpsi(n, r2), _chi(n, r2), _dchi(n, r2)
+        Aa = (Da * p1 - dp1) / (Da * c1 - dc1)
+        Ab = (Db * p1 - dp1) / (Db * c1 - dc1)
+        Da = (dp2 - Aa * dc2) / (p2 - Aa * c2)
+        Db = (dp2 - Ab * dc2) / (p2 - Ab * c2)
+    m = ms[-1]
+    psy, dpsy = _psi(n, y), _dpsi(n, y)
+    xi = y * (spherical_jn(n, y) + 1j * spherical_yn(n, y))
+    dxi = dpsy + 1j * (spherical_yn(n, y) + y * spherical_yn(n, y, derivative=True))
+    ta, tb = Da / m, m * Db
+    a = (ta * psy - dpsy) / (ta * xi - dxi)
+    b = (tb * psy - dpsy) / (tb * xi - dxi)
+    return a, b
+
+
 def amplitudes(a, b, theta):
     """S1(theta), S2(theta) from the angular functions pi_n, tau_n."""
     mu = np.cos(np.atleast_1d(theta))
@@ -113,8 +156,16 @@ def efficiencies(a, b, x):
     return qext, qsca
 
 
-def rcs_sphere(radius: float, eps_r: complex, theta, phi, k0: float = 2 * np.pi, core=None):
-    """Bistatic RCS (lambda0^2) of a sphere, or of a shell when core = (r_in, eps_core)."""
+def rcs_sphere(radius: float, eps_r: complex, theta, phi, k0: float = 2 * np.pi, core=None, layers=None):
+    """Bistatic RCS (lambda0^2) of a sphere, of a shell when core = (r_in, eps_core), or of a
+    multilayer sphere when layers = [(outer radius, eps_r), ...] from the innermost out (then
+    radius and eps_r are ignored)."""
+    if layers is not None:
+        xs = [k0 * r for r, _ in layers]
+        a, b = coefficients_multilayer(xs, [refractive_index(e) for _, e in layers])
+        S1, S2 = amplitudes(a, b, theta)
+        phi = np.asarray(phi, dtype=np.float64)
+        return 4 * np.pi / k0 ** 2 * (np.abs(S2) ** 2 * np.cos(phi) ** 2 + np.abs(S1) ** 2 * np.sin(phi) ** 2)
     m2 = refractive_index(eps_r)
     y = k0 * radius
     if core is None:

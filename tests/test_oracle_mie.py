@@ -61,3 +61,27 @@ def test_coated_reduces_to_homogeneous():
     # vacuum core of vanishing size -> homogeneous sphere of the shell index
     a3, b3 = mie.coefficients_coated(1e-4, x, 1.0 + 0j, m)
     assert np.abs(a3 - a2).max() < 1e-8 and np.abs(b3 - b2).max() < 1e-8
+
+
+def test_multilayer_reduces_to_homogeneous_and_coated():
+    """Equal layers give the homogeneous sphere; two layers give the Aden-Kerker coated sphere
+    (an independent formula); a vacuum core gives the shell."""
+    m = mie.refractive_index(4.0 - 0.3j)
+    a0, b0 = mie.coefficients_homogeneous(3.0, m)
+    a1, b1 = mie.coefficients_multilayer([1.0, 2.2, 3.0], [m, m, m], nmax=len(a0))
+    assert np.allclose(a1, a0, rtol=1e-9, atol=1e-13) and np.allclose(b1, b0, rtol=1e-9, atol=1e-13)
+    for m1, m2 in ((mie.refractive_index(6.0), mie.refractive_index(2.0 - 0.1j)),
+                   (1.0 + 0j, mie.refractive_index(-2.2 - 0.16j)),
+                   (mie.refractive_index(2.0), mie.refractive_index(5.0))):
+        a0, b0 = mie.coefficients_coated(1.4, 2.5, m1, m2)
+        a1, b1 = mie.coefficients_multilayer([1.4, 2.5], [m1, m2], nmax=len(a0))
+        assert np.allclose(a1, a0, rtol=1e-8, atol=1e-12) and np.allclose(b1, b0, rtol=1e-8, atol=1e-12)
+
+
+def test_multilayer_lossless_optical_theorem():
+    """Five lossless layers (eps 6 .. 2 from the centre out): Q_ext = Q_sca."""
+    xs = 2 * np.pi * np.array([0.1, 0.2, 0.3, 0.4, 0.5])
+    ms = [mie.refractive_index(e) for e in (6.0, 5.0, 4.0, 3.0, 2.0)]
+    a, b = mie.coefficients_multilayer(xs, ms)
+    qext, qsca = mie.efficiencies(a, b, xs[-1])
+    assert abs(qext - qsca) < 1e-10 * qext

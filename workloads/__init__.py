@@ -137,6 +137,33 @@ def layered_eps(body: VoxelBody, radii, eps_values) -> VoxelBody:
     return VoxelBody(body.name + "_layered", body.h, body.ijk, eps)
 
 
+def five_layer_sphere(h: float = 1.0 / 20) -> VoxelBody:
+    """Five concentric layers of thickness 0.1 lambda0 (outer radius 0.5), eps_r 2, 3, 4, 5, 6
+    from the outside in: the layered-sphere geometry of Sec. IV-A at a GPU-test size."""
+    radii = [0.5, 0.4, 0.3, 0.2, 0.1]
+    return layered_eps(sphere(radii[0], 2.0, h, name="five_layer_sphere"), radii, [2.0, 3.0, 4.0, 5.0, 6.0])
+
+
+def two_shell_sphere(h: float = 1.0 / 20) -> VoxelBody:
+    """Hollow sphere of two shells (outer radius 0.8, each 0.15 lambda0 thick), eps_r 4 inside and
+    2 outside, vacuum core (not meshed): the two-shell geometry of Sec. IV-A at a GPU-test size."""
+    body = shell(0.8, 0.5, 2.0, h, name="two_shell_sphere")
+    return layered_eps(body, [0.8, 0.65], [2.0, 4.0])
+
+
+def equal_volume_layers(h: float, radii):
+    """Radii of the spheres with the volume of the grid voxels (pitch h, centres (i + 1/2) h)
+    whose centres lie inside each radius: the staircase's equal-volume layer radii."""
+    out = []
+    for R in radii:
+        n = int(math.ceil(R / h)) + 1
+        c = (np.arange(-n, n, dtype=np.float64) + 0.5) * h
+        x, y, z = np.meshgrid(c, c, c, indexing="ij")
+        cnt = np.count_nonzero(x * x + y * y + z * z < R * R)
+        out.append((3.0 * cnt * h ** 3 / (4.0 * math.pi)) ** (1.0 / 3.0))
+    return out
+
+
 # --------------------------------------------------------------------------------------
 # Seeded vectors and excitations
 # --------------------------------------------------------------------------------------
