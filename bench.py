@@ -62,8 +62,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload(radius: float):
-    """Homogeneous sphere of the given radius, eps_r = 4 - 0.1j, pitch lambda0/10 (radius 2: N = 410,208)."""
+def workload(radius: float, kind: str = "sphere"):
+    """The body of an apply benchmark.
+
+    sphere: homogeneous sphere of the given radius, eps_r = 4 - 0.1j, pitch lambda0/10
+            (radius 2: N = 410,208, the benchmark workload);
+    shell:  Drude plasma shell 1.5/1.2 lambda0, vacuum core, pitch lambda0/20 (N = 690,768);
+    cube:   5 lambda0 cube, eps_r = 1 + 49 Phi(GRF), pitch lambda0/10 (N = 1,515,000)."""
+    if kind == "shell":
+        return W.plasma_shell(), ("plasma shell 1.5/1.2 lambda0, Drude eps_r=-2.2319-0.1616j, vacuum core, "
+                                  "pitch lambda0/20, N={n}")
+    if kind == "cube":
+        return W.cube_grf(5.0, 0.1), ("cube 5 lambda0, eps_r=1+49*Phi(GRF, corr 0.5, seed 20211101), "
+                                      "pitch lambda0/10, N={n}")
     body = W.sphere(radius, 4.0 - 0.1j, 1.0 / 10, name=f"sphere_r{radius:g}_eps4-0.1j")
     desc = f"sphere r={radius:g} lambda0, eps_r=4-0.1j, pitch lambda0/10, 6 Kuhn tets/voxel, N={{n}}"
     return body, desc
@@ -351,6 +362,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--radius", type=float, default=2.0,
                     help="sphere radius in wavelengths (2.0 = the benchmark workload; smaller for checks/profiles)")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "shell", "cube"],
+                    help="sphere (default, the benchmark workload), shell (plasma shell) or cube (GRF cube)")
+    ap.add_argument("--chi-con", type=float, default=1e-4, help="compression tolerance of Z")
     ap.add_argument("--nrhs", type=int, default=1,
                     help="right-hand sides per apply (>= 16 runs the tensor-core path)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -380,9 +394,9 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     hbm, peak_kind = peaks()
-    body, desc = workload(args.radius)
+    body, desc = workload(args.radius, args.workload)
     t0 = time.perf_counter()
-    op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=(1e-1 if args.zinv else 0.0), leaf=64,
+    op = pkg.Operator(body, W.K0, tol_con=args.chi_con, tol_fact=(1e-1 if args.zinv else 0.0), leaf=64,
                       factor_dtype="c64", seed=1)
     build_s = time.perf_counter() - t0
     tune = op.autotune(pkg.VIE_OP_Z) if nrhs_for_tune(args) else None
@@ -452,7 +466,7 @@ def main():
             "metric": METRIC if nrhs == 1 else METRIC.replace("single RHS", f"{nrhs} RHS"), "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": desc.format(n=n), "n": n, "levels": st.levels, "chi_con": 1e-4, "leaf": 64, "nrhs": nrhs,
+            "config": {"workload": desc.format(n=n), "n": n, "levels": st.levels, "chi_con": args.chi_con, "leaf": 64, "nrhs": nrhs,
                        "factor_entries": E, "factor_bytes_stored": int(sbytes.sum()), "max_rank": st.max_rank,
                        "build_seconds": round(build_s, 2),
                        "autotuned_tiling": None if tune is None else [int(c) for c in tune],

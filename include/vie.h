@@ -183,6 +183,19 @@ vie_status vie_solve(vie_op* op, const void* V, void* I, int64_t nrhs, double rt
                      int32_t restart, int32_t max_iter, int32_t* iters, double* relres,
                      void* stream);
 
+/* Solve the left-preconditioned system Zinv Z I = Zinv V (Eq. 6; M = I when
+ * the operator has no Zinv) with TFQMR (the paper's solver, Sec. II).  A
+ * column stops when the quasi-residual bound tau sqrt(m + 1) (m half-steps)
+ * falls below rtol ||M V|| and the true preconditioned residual
+ * ||M (V - Z I)|| / ||M V|| confirms rtol; otherwise it restarts from its
+ * iterate.  V, I: device c128 N x nrhs (ld = N).  iters (host, may be NULL):
+ * TFQMR iterations per column (two applications of Zinv Z each).  relres
+ * (host, may be NULL): the unpreconditioned ||V - Z I|| / ||V||.  Returns
+ * VIE_ENOTCONV (I holds the last iterate) when a column misses rtol within
+ * max_iter iterations, VIE_ENAN for a non-finite V. */
+vie_status vie_solve_tfqmr(vie_op* op, const void* V, void* I, int64_t nrhs, double rtol,
+                           int32_t max_iter, int32_t* iters, double* relres, void* stream);
+
 /* Bistatic RCS sigma(dir_k) for each column of I (device c128 N x nrhs) and
  * each unit direction dirs (host 3*ndir): rcs (host, ndir x nrhs, column
  * major), in lambda0^2, sigma = k0^4/(4 pi) |(I - rr) . F|^2,

@@ -23,7 +23,7 @@ VIE_OP_Z, VIE_OP_ZINV = 0, 1
 VIE_C64, VIE_C128 = 0, 1
 
 # every symbol declared in include/vie.h
-EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_farfield",
+EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_solve_tfqmr", "vie_farfield",
            "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_wait_selftest", "vie_destroy", "vie_last_error",
            "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy"]
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
         "vie_autotune": [P, I32, P, I32, P],
         "vie_rhs_planewave": [P, P, P, I64, P, P],
         "vie_solve": [P, P, P, I64, D, I32, I32, P, P, P],
+        "vie_solve_tfqmr": [P, P, P, I64, D, I32, P, P, P],
         "vie_farfield": [P, P, I64, P, I64, P, P],
         "vie_mesh_faces": [P, P, P, P],
         "vie_mesh_host": [P, I32, P, P, P, P, P, P],
@@ -287,6 +288,21 @@ class Operator:
         rel = np.zeros(nrhs, dtype=np.float64)
         st = _lib.vie_solve(self._h, ctypes.c_void_p(Vc.data_ptr()), ctypes.c_void_p(I.data_ptr()), nrhs,
                             float(rtol), restart, max_iter, iters.ctypes.data, rel.ctypes.data, _stream_ptr(stream))
+        if st not in (VIE_OK, VIE_ENOTCONV):
+            _check(st)
+        return I, iters, rel, st
+
+    def solve_tfqmr(self, V, rtol=1e-3, max_iter=500, stream=None):
+        """Left-preconditioned TFQMR (Eq. 6); returns (I, iterations, true relative residual, status)."""
+        import torch
+
+        Vc, nrhs, ld = _colmajor(V.to(torch.complex128), self.n)
+        assert ld == self.n
+        I = torch.empty((nrhs, self.n), dtype=torch.complex128, device=V.device).t()
+        iters = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        st = _lib.vie_solve_tfqmr(self._h, ctypes.c_void_p(Vc.data_ptr()), ctypes.c_void_p(I.data_ptr()), nrhs,
+                                  float(rtol), max_iter, iters.ctypes.data, rel.ctypes.data, _stream_ptr(stream))
         if st not in (VIE_OK, VIE_ENOTCONV):
             _check(st)
         return I, iters, rel, st

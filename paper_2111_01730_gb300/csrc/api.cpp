@@ -357,4 +357,19 @@ vie_status vie_solve(vie_op* h, const void* V, void* I, int64_t nrhs, double rto
   return st;
 }
 
+vie_status vie_solve_tfqmr(vie_op* h, const void* V, void* I, int64_t nrhs, double rtol, int32_t max_iter,
+                           int32_t* iters, double* relres, void* stream) {
+  bool conv = true;
+  vie_status st = guarded([&] {
+    VIE_REQUIRE(h && V && I && nrhs >= 1, VIE_EINVAL, "bad argument");
+    VIE_REQUIRE(rtol > 0 && max_iter >= 1, VIE_EINVAL, "bad tolerance or iteration limit");
+    solve_tfqmr(h, (const double2*)V, (double2*)I, nrhs, rtol, max_iter, iters, relres, (cudaStream_t)stream, conv);
+  });
+  if (st == VIE_OK && !conv) {
+    set_error("TFQMR stopped before reaching rtol");
+    return VIE_ENOTCONV;
+  }
+  return st;
+}
+
 }  // extern "C"

@@ -238,7 +238,7 @@ size_t tc_smem_bytes();
 void wait_timeout_check(uint32_t spins, int* d_status, cudaStream_t s);
 constexpr int kTcMinRhs = 16;
 constexpr size_t kGraphCache = 8;
-constexpr int64_t kDenseInverseLimit = 32768;  // largest diagonal block formed densely by the inverse builder   // the tensor-core path serves nrhs >= 16 (c64 factors and vectors)
+constexpr int64_t kDenseInverseLimit = 65536;  // largest diagonal block formed densely by the inverse builder
 
 void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles);
 void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles, int64_t max_tile_bytes, int vec_target);
@@ -296,6 +296,8 @@ void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res);
 void ensure_ws(vie_op* h, const Program& p, int64_t nrhs, int dtype);
 void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dtype, cudaStream_t s);
 void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int restart, int max_iter,
+                 int32_t* iters_out, double* relres_out, cudaStream_t s, bool& converged_all);
+void solve_tfqmr(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int max_iter,
                  int32_t* iters_out, double* relres_out, cudaStream_t s, bool& converged_all);
 void farfield_impl(const Geometry& g, const int32_t* d_tet_faces, const double2* I, int nrhs, const double* dirs,
                    int ndir, double* rcs, cudaStream_t s);

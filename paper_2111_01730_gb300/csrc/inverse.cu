@@ -9,15 +9,17 @@
 //
 // Construction here: for each node tau, E_tau is formed densely in complex
 // FP32 from its plain definition, E_tau = D_tau^-1 diag(D_tau1, D_tau2) - I
-// (the same matrix as above), with D_tau = Z(tau, tau) from the FP64 entry
-// evaluator, an LU factorization for D_tau^-1 and two GEMMs; it is then
-// compressed by the same ID-based butterfly construction as Z (Eqs. 7-10),
-// reading its entries from the dense matrix.  This replaces the randomized
-// recompression (BF_random_matvec inside BF_SMW, Algorithm 2) and is limited
-// by the dense blocks: levels whose nodes hold more than kDenseInverseLimit
-// unknowns are skipped, so that for large N the inverse is exact to chi_fact
-// inside the subtrees below that level and block diagonal above it.
-#include <cublas_v2.h>
+// (the same matrix as above), with D_tau = Z(tau, tau) from the entry
+// evaluator: an LU factorization of D_tau and a two-sided triangular solve
+// with diag(D_tau1, D_tau2) as right-hand sides (two n x n matrices per node).
+// It is then compressed by the same ID-based butterfly construction as Z
+// (Eqs. 7-10), reading its entries from the dense matrix.  This replaces the
+// randomized recompression (BF_random_matvec inside BF_SMW, Algorithm 2) and
+// is limited by the dense blocks: a level joins the inverse when its largest
+// node fits twice in the free device memory and holds at most
+// kDenseInverseLimit unknowns; above the first level that does not, the
+// inverse is block diagonal.  Nodes of a level are compressed in batches
+// whose dense E_tau fit in memory together.
 #include <cusolverDn.h>
 
 #include <chrono>
@@ -26,11 +28,6 @@
 
 namespace vie {
 
-#define VIE_CUBLAS(call)                                                                      \
-  do {                                                                                        \
-    cublasStatus_t st_ = (call);                                                              \
-    if (st_ != CUBLAS_STATUS_SUCCESS) throw Error{VIE_ECUDA, std::string(#call) + " failed"}; \
-  } while (0)
 #define VIE_CUSOLVER(call)                                                                      \
   do {                                                                                          \
     cusolverStatus_t st_ = (call);                                                              \
@@ -159,28 +156,31 @@ void dense_inverse(cusolverDnHandle_t sol, float2* D, float2* Dinv, int64_t n, c
 void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
   const Tree& t = h->tree;
   const int LH = t.levels;
-  const int64_t N = h->mesh.nf;
-  // Levels whose diagonal blocks exceed the dense limit are left out: the inverse
-  // then stops at level l_min (block diagonal over the level-l_min subtrees).
+  size_t free_b = 0, total_b = 0;
+  VIE_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  // room for the dense matrices: what is free now, less a margin for the ID
+  // builder's scratch, the solver workspace and the factors being built
+  const int64_t margin = int64_t(24) << 30;
+  const int64_t room = std::max<int64_t>(0, (int64_t)free_b - margin);
+  auto level_max = [&](int l) {
+    int64_t big = 0;
+    for (size_t i = 0; i + 1 < t.bounds[l].size(); ++i) big = std::max<int64_t>(big, t.bounds[l][i + 1] - t.bounds[l][i]);
+    return big;
+  };
   int l_min = 0;
   while (l_min < LH) {
-    int64_t big = 0;
-    for (size_t i = 0; i + 1 < t.bounds[l_min].size(); ++i) big = std::max<int64_t>(big, t.bounds[l_min][i + 1] - t.bounds[l_min][i]);
-    if (big <= kDenseInverseLimit) break;
+    const int64_t big = level_max(l_min);
+    if (big <= kDenseInverseLimit && 2 * big * big * (int64_t)sizeof(float2) <= room) break;
     ++l_min;
   }
   h->zinv_top_level = l_min;
   cusolverDnHandle_t sol = nullptr;
-  cublasHandle_t blas = nullptr;
   VIE_CUSOLVER(cusolverDnCreate(&sol));
-  VIE_CUBLAS(cublasCreate(&blas));
-  struct Handles {
+  struct Handle {
     cusolverDnHandle_t s;
-    cublasHandle_t b;
-    ~Handles() { if (s) cusolverDnDestroy(s); if (b) cublasDestroy(b); }
-  } hd{sol, blas};
+    ~Handle() { if (s) cusolverDnDestroy(s); }
+  } hd{sol};
   VIE_CUSOLVER(cusolverDnSetStream(sol, s));
-  VIE_CUBLAS(cublasSetStream(blas, s));
   Program& P = h->zinv;
   P.stages.clear();
   P.ncoef = 0;
@@ -201,42 +201,61 @@ void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
     }
     build_program(h, {}, src, h->cfg.tol_fact, P, /*leaf_blocks=*/true, SP_X, s, res);
   }
-  // levels L_H - 1 .. 0: E_tau = D_tau^-1 diag(D_tau1, D_tau2) - I, compressed at chi_fact
+  // levels L_H - 1 .. l_min: E_tau = D_tau^-1 diag(D_tau1, D_tau2) - I, compressed at chi_fact
   for (int l = LH - 1; l >= l_min; --l) {
     const auto& b = t.bounds[l];
     const auto& bc = t.bounds[l + 1];
     const int64_t nn = (int64_t)b.size() - 1;
-    std::vector<DevBuf> E(nn);
-    DenseSource src;
-    std::vector<BfSpec> specs;
-    for (int64_t i = 0; i < nn; ++i) {
-      const int64_t a = b[i], n = b[i + 1] - b[i];
-      const int64_t n1 = bc[2 * i + 1] - bc[2 * i], n2 = n - n1;
-      DevBuf D, Dl, Dinv;
-      D.alloc(sizeof(float2) * n * n);
-      Dl.alloc(sizeof(float2) * n * n);
-      Dinv.alloc(sizeof(float2) * n * n);
-      dense_block(h, a, n, D.as<float2>(), s);
-      VIE_CUDA(cudaMemcpyAsync(Dl.p, D.p, sizeof(float2) * n * n, cudaMemcpyDeviceToDevice, s));
-      dense_inverse(sol, Dl.as<float2>(), Dinv.as<float2>(), n, s);
-      E[i].alloc(sizeof(float2) * n * n);
-      const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-      float2* Dp = D.as<float2>();
-      float2* Ip = Dinv.as<float2>();
-      float2* Ep = E[i].as<float2>();
-      // E(:, 0:n1) = Dinv(:, 0:n1) D(0:n1, 0:n1);  E(:, n1:n) = Dinv(:, n1:n) D(n1:n, n1:n)
-      VIE_CUBLAS(cublasCgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)n1, (int)n1, &one, (const cuComplex*)Ip,
-                             (int)n, (const cuComplex*)Dp, (int)n, &zero, (cuComplex*)Ep, (int)n));
-      VIE_CUBLAS(cublasCgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)n2, (int)n2, &one,
-                             (const cuComplex*)(Ip + n1 * n), (int)n, (const cuComplex*)(Dp + n1 * n + n1), (int)n,
-                             &zero, (cuComplex*)(Ep + n1 * n), (int)n));
-      sub_identity<<<grid_for(n), 256, 0, s>>>(Ep, n);
-      VIE_CUDA(cudaGetLastError());
+    const int64_t big = level_max(l);
+    // E_tau of a batch stay resident until the batch is compressed; one D_tau at a time
+    const int64_t batch_room = room - big * big * (int64_t)sizeof(float2);
+    for (int64_t i0 = 0; i0 < nn;) {
+      std::vector<DevBuf> E;
+      DenseSource src;
+      std::vector<BfSpec> specs;
+      int64_t used = 0;
+      int64_t i = i0;
+      for (; i < nn; ++i) {
+        const int64_t a = b[i], n = b[i + 1] - b[i];
+        const int64_t bytes = n * n * (int64_t)sizeof(float2);
+        if (i > i0 && used + bytes > batch_room) break;
+        const int64_t n1 = bc[2 * i + 1] - bc[2 * i], n2 = n - n1;
+        DevBuf D, ipiv, info, work;
+        D.alloc(bytes);
+        E.emplace_back();
+        E.back().alloc(bytes);
+        used += bytes;
+        float2* Dp = D.as<float2>();
+        float2* Ep = E.back().as<float2>();
+        dense_block(h, a, n, Dp, s);
+        // E = diag(D_tau1, D_tau2) before D is factored in place
+        VIE_CUDA(cudaMemsetAsync(Ep, 0, bytes, s));
+        VIE_CUDA(cudaMemcpy2DAsync(Ep, sizeof(float2) * n, Dp, sizeof(float2) * n, sizeof(float2) * n1, n1,
+                                   cudaMemcpyDeviceToDevice, s));
+        VIE_CUDA(cudaMemcpy2DAsync(Ep + n1 * n + n1, sizeof(float2) * n, Dp + n1 * n + n1, sizeof(float2) * n,
+                                   sizeof(float2) * n2, n2, cudaMemcpyDeviceToDevice, s));
+        int lwork = 0;
+        VIE_CUSOLVER(cusolverDnCgetrf_bufferSize(sol, (int)n, (int)n, (cuComplex*)Dp, (int)n, &lwork));
+        work.alloc(sizeof(cuComplex) * std::max(lwork, 1));
+        ipiv.alloc(sizeof(int) * n);
+        info.alloc(sizeof(int));
+        VIE_CUSOLVER(cusolverDnCgetrf(sol, (int)n, (int)n, (cuComplex*)Dp, (int)n, work.as<cuComplex>(),
+                                      ipiv.as<int>(), info.as<int>()));
+        VIE_CUSOLVER(cusolverDnCgetrs(sol, CUBLAS_OP_N, (int)n, (int)n, (const cuComplex*)Dp, (int)n, ipiv.as<int>(),
+                                      (cuComplex*)Ep, (int)n, info.as<int>()));
+        int hinfo = 0;
+        VIE_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        VIE_CUDA(cudaStreamSynchronize(s));
+        VIE_REQUIRE(hinfo == 0, VIE_ENAN, "singular diagonal block in the inverse construction");
+        sub_identity<<<grid_for(n), 256, 0, s>>>(Ep, n);
+        VIE_CUDA(cudaGetLastError());
+        src.refs.push_back(DenseRef{Ep, a, n});
+        specs.push_back(BfSpec{l, i, i, (int)(i - i0)});
+      }
       VIE_CUDA(cudaStreamSynchronize(s));
-      src.refs.push_back(DenseRef{Ep, a, n});
-      specs.push_back(BfSpec{l, i, i, (int)i});
+      build_program(h, specs, src, h->cfg.tol_fact, P, /*leaf_blocks=*/false, SP_Y, s, res);
+      i0 = i;
     }
-    build_program(h, specs, src, h->cfg.tol_fact, P, /*leaf_blocks=*/false, SP_Y, s, res);
   }
   h->has_zinv = true;
 }

@@ -1,4 +1,5 @@
-// Solve driver: right-preconditioned restarted GMRES inside FP64 iterative refinement.
+// Solve drivers: right-preconditioned restarted GMRES inside FP64 iterative
+// refinement, and the paper's left-preconditioned TFQMR.
 //
 // The paper solves the preconditioned system (Eq. 6) with TFQMR; the reading
 // used here is right preconditioning, Z M u = r, x = M u, with M = Zinv when
@@ -142,6 +143,35 @@ __global__ void has_nonfinite(const double2* a, int64_t n, int* flag) {
 }
 
 int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 8); }
+
+// out[c] = a(c)^H b(c), one CTA per column
+__global__ void coldot(const double2* a, const double2* b, int64_t n, double2* out) {
+  const int c = blockIdx.x;
+  const double2* x = a + (int64_t)c * n;
+  const double2* y = b + (int64_t)c * n;
+  double re = 0, im = 0;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+    re += x[t].x * y[t].x + x[t].y * y[t].y;
+    im += x[t].x * y[t].y - x[t].y * y[t].x;
+  }
+  __shared__ double sr[256], si[256];
+  sr[threadIdx.x] = re;
+  si[threadIdx.x] = im;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) { sr[threadIdx.x] += sr[threadIdx.x + k]; si[threadIdx.x] += si[threadIdx.x + k]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = make_double2(sr[0], si[0]);
+}
+
+// out(c) = a(c) + cb[c] * b(c)   (out may alias a or b)
+__global__ void axpby_col(const double2* a, const double2* b, const double2* cb, double2* out, int64_t n, int nrhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 k = cb[e / n], u = a[e], v = b[e];
+    out[e] = make_double2(u.x + k.x * v.x - k.y * v.y, u.y + k.x * v.y + k.y * v.x);
+  }
+}
 
 }  // namespace
 
@@ -336,6 +366,203 @@ void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, doub
     converged_all &= rel[c] <= rtol;
   }
   VIE_CUDA(cudaMemcpyAsync(x_out, ws.x.p, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
+  VIE_CUDA(cudaStreamSynchronize(s));
+}
+
+// Left-preconditioned TFQMR (Freund 1993) on M Z I = M V (Eq. 6), M = Zinv
+// when the operator carries one.  Per iteration: y2 = y1 - alpha v, two
+// quasi-residual half-steps (w -= alpha A y; theta = ||w|| / tau;
+// c = 1 / sqrt(1 + theta^2); tau *= theta c; d = y + theta_prev^2 eta_prev /
+// alpha d; eta = c^2 alpha; x += eta d), then beta = rho_new / rho,
+// y1 = w + beta y2 and v = A y1 + beta (A y2 + beta v): two applications of
+// A = M Z.  A column stops when tau sqrt(m + 1) <= rtol ||M V|| (m = half-steps),
+// and the true preconditioned residual, applied with FP64 vectors, decides
+// whether it restarts from its iterate.  Inside the recurrence the applies of
+// a C32 operator run on complex FP32 vectors; vectors and scalars are FP64.
+// All columns step together through batched multi-column applies; a stopped
+// column gets zero coefficients so that its iterate stays fixed.
+void solve_tfqmr(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int max_iter,
+                 int32_t* iters_out, double* relres_out, cudaStream_t s, bool& converged_all) {
+  const int64_t n = h->mesh.nf;
+  const int64_t nb = n * nrhs;
+  const bool fp64 = h->cfg.factor_dtype == VIE_C128;
+  const bool pre = h->has_zinv;
+  DevBuf bx, bmb, brt, bw, by1, by2, bay1, bay2, bv, bd, bt, bt2, bva, bvb, bcoef, bdot, bnrm, bflag;
+  for (DevBuf* p : {&bx, &bmb, &brt, &bw, &by1, &by2, &bay1, &bay2, &bv, &bd, &bt, &bt2}) p->alloc(sizeof(double2) * nb);
+  bva.alloc((fp64 ? sizeof(double2) : sizeof(float2)) * nb);
+  bvb.alloc((fp64 ? sizeof(double2) : sizeof(float2)) * nb);
+  bcoef.alloc(sizeof(double2) * nrhs);
+  bdot.alloc(sizeof(double2) * nrhs);
+  bnrm.alloc(sizeof(double) * nrhs);
+  bflag.alloc(sizeof(int));
+  const int G = grid_for(nb);
+  double2 *x = bx.as<double2>(), *mb = bmb.as<double2>(), *rt = brt.as<double2>(), *w = bw.as<double2>();
+  double2 *y1 = by1.as<double2>(), *y2 = by2.as<double2>(), *Ay1 = bay1.as<double2>(), *Ay2 = bay2.as<double2>();
+  double2 *v = bv.as<double2>(), *d = bd.as<double2>(), *t = bt.as<double2>(), *t2 = bt2.as<double2>();
+  double2* coef = bcoef.as<double2>();
+  VIE_CUDA(cudaMemsetAsync(bflag.p, 0, sizeof(int), s));
+  has_nonfinite<<<G, 256, 0, s>>>(b, nb, bflag.as<int>());
+  int flag = 0;
+  VIE_CUDA(cudaMemcpyAsync(&flag, bflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA(cudaStreamSynchronize(s));
+  VIE_REQUIRE(!flag, VIE_ENAN, "right-hand side holds NaN or Inf");
+
+  // out = A u inside the recurrence (C32 applies for a C32 operator)
+  auto applyA = [&](const double2* u, double2* out) {
+    if (fp64) {
+      if (pre) {
+        op_apply(h, VIE_OP_Z, u, bva.p, nrhs, VIE_C128, s);
+        op_apply(h, VIE_OP_ZINV, bva.p, out, nrhs, VIE_C128, s);
+      } else {
+        op_apply(h, VIE_OP_Z, u, out, nrhs, VIE_C128, s);
+      }
+    } else {
+      to_c64<<<G, 256, 0, s>>>(u, bva.as<float2>(), nb);
+      op_apply(h, VIE_OP_Z, bva.p, bvb.p, nrhs, VIE_C64, s);
+      float2* r = bvb.as<float2>();
+      if (pre) {
+        op_apply(h, VIE_OP_ZINV, bvb.p, bva.p, nrhs, VIE_C64, s);
+        r = bva.as<float2>();
+      }
+      to_c128<<<G, 256, 0, s>>>(r, out, nb);
+    }
+  };
+  // out = M u with FP64 vectors (C32 or FP64 factors)
+  auto applyM = [&](const double2* u, double2* out) {
+    if (pre) op_apply(h, VIE_OP_ZINV, u, out, nrhs, VIE_C128, s);
+    else VIE_CUDA(cudaMemcpyAsync(out, u, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
+  };
+  auto norms = [&](const double2* a, std::vector<double>& out) {
+    col_norm2<<<(int)nrhs, 256, 0, s>>>(a, n, bnrm.as<double>());
+    VIE_CUDA(cudaMemcpyAsync(out.data(), bnrm.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    for (double& q : out) q = std::sqrt(q);
+  };
+  auto dotc = [&](const double2* a, const double2* bb, std::vector<cd>& out) {
+    coldot<<<(int)nrhs, 256, 0, s>>>(a, bb, n, bdot.as<double2>());
+    std::vector<double2> hv(nrhs);
+    VIE_CUDA(cudaMemcpyAsync(hv.data(), bdot.p, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    for (int64_t c = 0; c < nrhs; ++c) out[c] = cd(hv[c].x, hv[c].y);
+  };
+  // out = a + k[c] b
+  auto axpby = [&](const double2* a, const std::vector<cd>& k, const double2* bb, double2* out) {
+    std::vector<double2> hk(nrhs);
+    for (int64_t c = 0; c < nrhs; ++c) hk[c] = make_double2(k[c].real(), k[c].imag());
+    VIE_CUDA(cudaMemcpyAsync(coef, hk.data(), sizeof(double2) * nrhs, cudaMemcpyHostToDevice, s));
+    axpby_col<<<G, 256, 0, s>>>(a, bb, coef, out, n, (int)nrhs);
+    VIE_CUDA(cudaStreamSynchronize(s));  // hk goes out of scope
+  };
+  // preconditioned residual r = M (b - Z x) into `out` (FP64 vectors)
+  auto pres = [&](double2* out) {
+    op_apply(h, VIE_OP_Z, x, t2, nrhs, VIE_C128, s);
+    sub<<<G, 256, 0, s>>>(b, t2, t2, nb);
+    applyM(t2, out);
+  };
+
+  VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * nb, s));
+  applyM(b, mb);
+  std::vector<double> nmb(nrhs), nr(nrhs), nw(nrhs);
+  norms(mb, nmb);
+  std::vector<int> its(nrhs, 0), want(nrhs, 0);
+  std::vector<double> prel(nrhs, 1.0);
+  for (int cycle = 0; cycle < 64; ++cycle) {
+    pres(t);  // r0 = M (b - Z x)
+    norms(t, nr);
+    bool any = false;
+    for (int64_t c = 0; c < nrhs; ++c) {
+      prel[c] = nmb[c] > 0 ? nr[c] / nmb[c] : 0.0;
+      want[c] = prel[c] > rtol && its[c] < max_iter;
+      any |= want[c] != 0;
+    }
+    if (!any) break;
+    const std::vector<int> its0(its);
+    std::vector<int> live(want);
+    VIE_CUDA(cudaMemcpyAsync(rt, t, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(w, t, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
+    VIE_CUDA(cudaMemcpyAsync(y1, t, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
+    VIE_CUDA(cudaMemsetAsync(d, 0, sizeof(double2) * nb, s));
+    applyA(y1, Ay1);
+    VIE_CUDA(cudaMemcpyAsync(v, Ay1, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> tau(nr), theta(nrhs, 0.0);
+    std::vector<cd> rho(nrhs), alpha(nrhs), sigma(nrhs), beta(nrhs), eta(nrhs, cd(0)), kd(nrhs), kx(nrhs), ka(nrhs);
+    std::vector<int> m(nrhs, 0);
+    for (int64_t c = 0; c < nrhs; ++c) rho[c] = cd(nr[c] * nr[c], 0.0);  // r~0 = r0
+    for (;;) {
+      dotc(rt, v, sigma);
+      bool alive = false;
+      for (int64_t c = 0; c < nrhs; ++c) {
+        if (live[c] && (std::abs(sigma[c]) == 0.0 || std::abs(rho[c]) == 0.0)) live[c] = 0;  // breakdown
+        alpha[c] = live[c] ? rho[c] / sigma[c] : cd(0);
+        ka[c] = -alpha[c];
+        alive |= live[c] != 0;
+      }
+      if (!alive) break;
+      axpby(y1, ka, v, y2);  // y2 = y1 - alpha v
+      applyA(y2, Ay2);
+      for (int64_t c = 0; c < nrhs; ++c) its[c] += live[c];
+      for (int half = 0; half < 2; ++half) {
+        const double2* y = half == 0 ? y1 : y2;
+        const double2* Ay = half == 0 ? Ay1 : Ay2;
+        axpby(w, ka, Ay, w);  // w -= alpha A y
+        norms(w, nw);
+        for (int64_t c = 0; c < nrhs; ++c) {
+          kd[c] = kx[c] = cd(0);
+          if (!live[c]) continue;
+          m[c] += 1;
+          const double th_prev = theta[c];
+          const cd eta_prev = eta[c];
+          theta[c] = tau[c] > 0 ? nw[c] / tau[c] : 0.0;
+          const double cc = 1.0 / std::sqrt(1.0 + theta[c] * theta[c]);
+          tau[c] = tau[c] * theta[c] * cc;
+          kd[c] = th_prev * th_prev * eta_prev / alpha[c];
+          eta[c] = cc * cc * alpha[c];
+          kx[c] = eta[c];
+          if (tau[c] * std::sqrt((double)m[c] + 1.0) <= rtol * nmb[c]) live[c] = 0;
+        }
+        axpby(y, kd, d, d);  // d = y + (theta_prev^2 eta_prev / alpha) d
+        axpby(x, kx, d, x);  // x += eta d
+        for (int64_t c = 0; c < nrhs; ++c) ka[c] = live[c] ? -alpha[c] : cd(0);
+      }
+      bool more = false;
+      for (int64_t c = 0; c < nrhs; ++c) {
+        if (its[c] >= max_iter) live[c] = 0;
+        more |= live[c] != 0;
+      }
+      if (!more) break;
+      std::vector<cd> rho_new(nrhs);
+      dotc(rt, w, rho_new);
+      for (int64_t c = 0; c < nrhs; ++c) {
+        beta[c] = live[c] ? rho_new[c] / rho[c] : cd(0);
+        if (live[c]) rho[c] = rho_new[c];
+      }
+      axpby(w, beta, y2, y1);  // y1 = w + beta y2
+      applyA(y1, Ay1);
+      axpby(Ay2, beta, v, t);  // t = A y2 + beta v
+      axpby(Ay1, beta, t, v);  // v = A y1 + beta t
+    }
+    bool progressed = false;
+    for (int64_t c = 0; c < nrhs; ++c) progressed |= its[c] > its0[c];
+    if (!progressed) break;  // breakdown before any step
+  }
+  pres(t);
+  norms(t, nr);
+  converged_all = true;
+  for (int64_t c = 0; c < nrhs; ++c) {
+    prel[c] = nmb[c] > 0 ? nr[c] / nmb[c] : 0.0;
+    converged_all &= prel[c] <= rtol;
+  }
+  if (relres_out) {  // true residual ||b - Z x|| / ||b||
+    std::vector<double> nbv(nrhs);
+    norms(b, nbv);
+    op_apply(h, VIE_OP_Z, x, t2, nrhs, VIE_C128, s);
+    sub<<<G, 256, 0, s>>>(b, t2, t2, nb);
+    norms(t2, nr);
+    for (int64_t c = 0; c < nrhs; ++c) relres_out[c] = nbv[c] > 0 ? nr[c] / nbv[c] : 0.0;
+  }
+  if (iters_out)
+    for (int64_t c = 0; c < nrhs; ++c) iters_out[c] = its[c];
+  VIE_CUDA(cudaMemcpyAsync(x_out, x, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, s));
   VIE_CUDA(cudaStreamSynchronize(s));
 }
 

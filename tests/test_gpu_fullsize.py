@@ -27,7 +27,8 @@ def full():
     op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=1e-1, leaf=64, factor_dtype="c64", seed=1)
     op.autotune()
     mesh = build_mesh(body)
-    return body, op, mesh
+    yield body, op, mesh
+    op.close()
 
 
 def test_sampled_rows_of_the_full_size_apply(full):
@@ -56,7 +57,8 @@ def test_full_size_apply_is_finite_and_linear(full):
 
 
 def test_full_size_solve_residual_rows_and_rcs_vs_mie(full):
-    """Right-preconditioned GMRES with FP64 refinement on the 410,208-unknown sphere: the residual
+    """Right-preconditioned GMRES with FP64 refinement to rtol 1e-3 (the paper's chi_sol for
+    dielectric spheres) on the 410,208-unknown sphere: the residual
     b - Z I on sampled rows with the oracle's exact rows of Z and b, and the bistatic RCS cuts
     against the Mie series of the equal-volume sphere (eps_r = 4 - 0.1j)."""
     body, op, mesh = full
@@ -64,11 +66,11 @@ def test_full_size_solve_residual_rows_and_rcs_vs_mie(full):
     k, p = W.planewave_x_along_z()
     V = op.rhs_planewave(k, p)
     t0 = time.time()
-    I, it, rel, st = op.solve(V, rtol=1e-5, restart=30, max_iter=400)
+    I, it, rel, st = op.solve(V, rtol=1e-3, restart=200, max_iter=1500)
     torch.cuda.synchronize()
     print("full-size solve: iterations", it[0], "relres", rel[0], "seconds", round(time.time() - t0, 2),
           "zinv top level", op.get_stats().zinv_top_level)
-    assert st == pkg.VIE_OK and rel[0] <= 1e-5
+    assert st == pkg.VIE_OK and rel[0] <= 1e-3
     Ih = I[:, 0].cpu().numpy()
     E = Elements(mesh, W.K0)
     rows = np.random.default_rng(11).choice(n, size=8, replace=False)

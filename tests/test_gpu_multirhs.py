@@ -42,3 +42,23 @@ def test_tensor_core_apply_deterministic(op_pair):
     b = op.apply(X).clone()
     op.check()
     assert torch.equal(a, b)
+
+
+@pytest.fixture(scope="module")
+def op_mid():
+    """Sphere r = 0.8 (N = 27,360): ranks up to ~300, so work items fill 128 output rows and
+    run many k-chunks, and each CTA streams several items through its copy ring."""
+    return pkg.Operator(W.sphere(0.8, 4.0 - 0.1j, 1.0 / 10), W.K0, tol_con=1e-4, leaf=64)
+
+
+@pytest.mark.parametrize("nrhs", [48, 128, 200])
+def test_tensor_core_apply_mid_size_matches_single_rhs(op_mid, nrhs):
+    op = op_mid
+    X = torch.from_numpy(W.random_block(op.n, nrhs, seed=100 + nrhs)).to(torch.complex64).cuda()
+    X = X.t().contiguous().t()
+    Y = op.apply(X)
+    op.check()
+    cols = [0, 1, nrhs // 2, nrhs - 1]
+    ref = torch.stack([op.apply(X[:, j].contiguous()) for j in cols], 1)
+    err = (torch.linalg.norm(Y[:, cols] - ref) / torch.linalg.norm(ref)).item()
+    assert err < 2e-5, err

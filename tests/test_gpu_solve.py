@@ -38,3 +38,32 @@ def test_solve_reports_nonconvergence_and_nan(lossy_sphere):
     with pytest.raises(pkg.VieError) as e:
         op.solve(V, rtol=1e-6)
     assert e.value.status == pkg.VIE_ENAN
+
+
+@pytest.mark.parametrize("tol_fact", [0.0, 1e-1])
+def test_tfqmr_matches_dense_lu(lossy_sphere, tol_fact):
+    """Left-preconditioned TFQMR (the paper's solver) with and without Zinv, three plane waves."""
+    body, E, Z = lossy_sphere["body"], lossy_sphere["E"], lossy_sphere["Z"]
+    op = pkg.Operator(body, W.K0, tol_con=1e-6, tol_fact=tol_fact, leaf=64)
+    k, p = W.planewave_random(3, seed=4)
+    V = op.rhs_planewave(k, p)
+    I, iters, rel, st = op.solve_tfqmr(V, rtol=1e-6, max_iter=400)
+    assert st == pkg.VIE_OK, (iters, rel)
+    Io = solve_dense(Z, rhs_planewave(E, k, p))
+    err = np.linalg.norm(I.cpu().numpy() - Io) / np.linalg.norm(Io)
+    print("TFQMR chi_fact", tol_fact, "iterations", iters, "true relres", rel, "error vs LU", err)
+    assert err < 1e-3, err
+    if tol_fact > 0:
+        assert iters.max() <= 10      # the preconditioner keeps TFQMR in single digits
+
+
+def test_tfqmr_reports_nonconvergence_and_nan(lossy_sphere):
+    op = pkg.Operator(lossy_sphere["body"], W.K0, tol_con=1e-4, leaf=64)
+    k, p = W.planewave_x_along_z()
+    V = op.rhs_planewave(k, p)
+    I, iters, rel, st = op.solve_tfqmr(V, rtol=1e-12, max_iter=3)
+    assert st == pkg.VIE_ENOTCONV and iters[0] == 3
+    V[3, 0] = float("nan")
+    with pytest.raises(pkg.VieError) as e:
+        op.solve_tfqmr(V, rtol=1e-6)
+    assert e.value.status == pkg.VIE_ENAN
