@@ -81,3 +81,26 @@ def test_five_layer_sphere_tfqmr_rcs_vs_multilayer_mie():
     # built here (sampled-row IDs of the dense E_tau, complex FP32) needs about 20
     assert st_.zinv_top_level == 0 and it[0] <= 30
     assert max(rmse) < 0.05
+
+
+def test_two_shell_sphere_tfqmr_rcs_vs_multilayer_mie():
+    """Two-shell geometry of Sec. IV-A at test size (vacuum core r = 0.3, shells eps 4 to 0.4 and
+    eps 2 to 0.5, pitch 1/20, N = 42,312): chi_fact 1e-1, TFQMR to chi_sol 1e-3, RCS against the
+    multilayer Mie series with a vacuum core."""
+    body = W.two_shell_sphere()
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=1e-1, leaf=64)
+    assert op.n == 42312
+    k, p = W.planewave_x_along_z()
+    I, it, rel, st = op.solve_tfqmr(op.rhs_planewave(k, p), rtol=1e-3, max_iter=200)
+    r0, r1, r2 = W.equal_volume_layers(body.h, [0.3, 0.4, 0.5])
+    layers = [(r0, 1.0), (r1, 4.0), (r2, 2.0)]
+    th = np.arange(0, 181, 2.0)
+    rmse = []
+    for ph in (0.0, 90.0):
+        g = op.farfield_rcs(I, cut_directions(th, ph))[:, 0]
+        m = rcs_sphere(0.0, 0.0, np.radians(th), np.radians(ph), layers=layers)
+        rmse.append(np.sqrt(np.mean((g - m) ** 2)) / m.max())
+    print("two-shell sphere: zinv top level", op.get_stats().zinv_top_level, "TFQMR iterations", it[0],
+          "relres", rel[0], "RCS relative RMSE", rmse)
+    assert st == pkg.VIE_OK and it[0] <= 30
+    assert max(rmse) < 0.05

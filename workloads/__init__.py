@@ -145,10 +145,10 @@ def five_layer_sphere(h: float = 1.0 / 20) -> VoxelBody:
 
 
 def two_shell_sphere(h: float = 1.0 / 20) -> VoxelBody:
-    """Hollow sphere of two shells (outer radius 0.8, each 0.15 lambda0 thick), eps_r 4 inside and
-    2 outside, vacuum core (not meshed): the two-shell geometry of Sec. IV-A at a GPU-test size."""
-    body = shell(0.8, 0.5, 2.0, h, name="two_shell_sphere")
-    return layered_eps(body, [0.8, 0.65], [2.0, 4.0])
+    """Hollow sphere of two 0.1 lambda0 shells (outer radius 0.5, vacuum core of radius 0.3, not
+    meshed), eps_r 4 inside and 2 outside: the two-shell geometry of Sec. IV-A at a GPU-test size."""
+    body = shell(0.5, 0.3, 2.0, h, name="two_shell_sphere")
+    return layered_eps(body, [0.5, 0.4], [2.0, 4.0])
 
 
 def equal_volume_layers(h: float, radii):
