@@ -40,6 +40,22 @@ UNIT = "GB/s"
 # profiles/stage1_kernel_sphere_r1.0.md (stages 1-3 at N = 52,584), scaled to a full apply.
 TRAFFIC_RATIO = 1.021
 TRAFFIC_NOTE = "ncu dram bytes of stage1_kernel stages 1-3 at r=1.0 (N=52,584) = 1.021 x algorithmic, scaled"
+# the same ratio for the shared-memory bulk-staged kernel (autotuner candidates 9-11); None until captured
+BULK_TRAFFIC_RATIO = None
+BULK_TRAFFIC_NOTE = "stage1_bulk_kernel changed since its last ncu capture"
+
+
+def single_rhs_kernels(tune):
+    """Kernel names and DRAM-traffic ratio of the single-RHS stages for an autotuner choice list
+    (candidates 0-8 stage1_kernel<4>, 9-11 stage1_bulk_kernel, 12-20 stage1_kernel<8>)."""
+    kinds = {"stage1_kernel<4>" if c < 9 else "stage1_bulk_kernel" if c < 12 else "stage1_kernel<8>"
+             for c in ([0] if tune is None else [int(c) for c in tune])}
+    names = " + ".join(sorted(kinds))
+    if kinds == {"stage1_kernel<4>"}:
+        return names, TRAFFIC_RATIO, TRAFFIC_NOTE
+    if kinds == {"stage1_bulk_kernel"}:
+        return names, BULK_TRAFFIC_RATIO, BULK_TRAFFIC_NOTE
+    return names, None, "no ncu capture of this kernel mix; traffic ratio not measured"
 
 
 def _bf16_peak():
@@ -369,6 +385,9 @@ def main():
                     help="right-hand sides per apply (>= 16 runs the tensor-core path)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default stage tiling")
+    ap.add_argument("--tiling", type=int, default=None,
+                    help="use one autotuner candidate on every stage (0-8 streaming kernel, 9-11 shared-memory "
+                         "bulk kernel, 12-20 streaming kernel with 8 loads in flight)")
     ap.add_argument("--zinv", action="store_true", help="also build Zinv (chi_fact 1e-1) and time its apply")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (solves/s, p50/p99 latency)")
     ap.add_argument("--requests", type=int, default=120)
@@ -399,7 +418,11 @@ def main():
     op = pkg.Operator(body, W.K0, tol_con=args.chi_con, tol_fact=(1e-1 if args.zinv else 0.0), leaf=64,
                       factor_dtype="c64", seed=1)
     build_s = time.perf_counter() - t0
-    tune = op.autotune(pkg.VIE_OP_Z) if nrhs_for_tune(args) else None
+    if args.tiling is not None:  # one fixed kernel/tiling candidate on every stage (profiling)
+        tune = np.full(op.get_stats().apply_stages_z, args.tiling, dtype=np.int32)
+        op.set_tiling(tune)
+    else:
+        tune = op.autotune(pkg.VIE_OP_Z) if nrhs_for_tune(args) else None
     st = op.get_stats()
     n = op.n
     entries, sbytes, tiles = op.program_info(pkg.VIE_OP_Z)
@@ -462,6 +485,7 @@ def main():
     achieved = stage_alg / (stage_ms.sum() * 1e-3) / 1e9
     useful_tflops = 8.0 * E * nrhs / (stage_ms.sum() * 1e-3) / 1e12
     if rank == 0:
+        k_names, k_ratio, k_note = single_rhs_kernels(tune)
         line = {
             "metric": METRIC if nrhs == 1 else METRIC.replace("single RHS", f"{nrhs} RHS"), "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -477,9 +501,10 @@ def main():
             "apply_latency_ms": {"p50": round(float(np.percentile(per, 50)), 4),
                                  "p99": round(float(np.percentile(per, 99)), 4)},
             "roofline": ({"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                          "frac": round(achieved / hbm, 4), "traffic": TRAFFIC_RATIO and round(TRAFFIC_RATIO * stage_alg),
-                          "traffic_note": TRAFFIC_NOTE,
-                          "kernel": "stage1_kernel (single-RHS stages, all launches of one apply)"} if nrhs < 16 else
+                          "frac": round(achieved / hbm, 4), "traffic": k_ratio and round(k_ratio * stage_alg),
+                          "traffic_note": k_note,
+                          "kernel": k_names + " (single-RHS stages, autotuned per stage; all launches of one apply)"}
+                         if nrhs < 16 else
                          {"bound": "tensor", "achieved": round(useful_tflops, 2), "peak": BF16_PEAK[0], "unit": "TFLOP/s",
                           "frac": round(useful_tflops / BF16_PEAK[0], 4), "traffic": None,
                           "peak_note": BF16_PEAK[1] + "; useful complex flops 8*E*nrhs (the BF16x3 split issues 3x)",

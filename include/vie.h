@@ -73,7 +73,7 @@ typedef struct {
   int32_t factor_dtype;/* vie_dtype of the stored factors (VIE_C64 default)     */
   uint64_t seed;       /* seed of the row sampling in the IDs                   */
   int32_t oversample;  /* extra random rows per ID beyond the candidate count   */
-  int32_t reserved;
+  int32_t id_tol_div;  /* each ID truncates at tol / id_tol_div (<= 1: at tol)  */
 } vie_config;
 
 typedef struct {
@@ -150,12 +150,35 @@ vie_status vie_apply_noalloc(vie_op* op, int32_t which, const void* X, void* Y, 
                              int64_t ldx, int64_t ldy, int32_t dtype, void* stream);
 
 /* Autotune the single-RHS apply (c64 factors): for every stage, time each
- * candidate tiling (maximum tile 4, 16 or 64 KB of factor data x 2, 4 or 8
- * 16-byte vectors per lane and row) with CUDA events on `stream` and keep the
- * fastest.  choice (host, cap >= stages, may be NULL) receives the index of the
- * chosen candidate per stage (tile-size index * 3 + vector index).  Results of
- * later applies are unchanged (tiling only moves work between warps). */
+ * candidate with CUDA events on `stream` and keep the fastest.  Candidates
+ * 0-8: the streaming kernel (four 16-byte loads in flight per lane) with a
+ * maximum tile of 4, 16 or 64 KB of factor data x 2, 4 or 8 16-byte vectors
+ * per lane and row (index = tile-size index * 3 + vector index); 9-11: the
+ * kernel that stages 32 KB tiles in shared memory by bulk asynchronous
+ * copies, with 2, 4 or 8 vectors per lane; 12-20: the streaming kernel with
+ * eight loads in flight per lane, tiles as in 0-8.  choice (host, cap >=
+ * stages, may be NULL) receives the chosen index per stage.  Results of
+ * later applies are unchanged (tiling and staging only move work between
+ * warps and memories; each output row keeps one owner). */
 vie_status vie_autotune(vie_op* op, int32_t which, int32_t* choice, int32_t cap, void* stream);
+
+/* Set the single-RHS kernel and tiling of every stage to the autotuner
+ * candidate choice[i] (host, n = the program's stage count; indices as in
+ * vie_autotune), e.g. to restore a saved tuning.  VIE_EINVAL for a wrong
+ * count, an index outside 0-20, c128 factors, or a bulk candidate whose tile
+ * does not fit its 32 KB slot. */
+vie_status vie_set_tiling(vie_op* op, int32_t which, const int32_t* choice, int32_t n, void* stream);
+
+/* Choose where multi-RHS applies (c64 vectors, c64 factors) switch from the
+ * SIMT kernel to the tensor cores: the stages of one apply are timed with 2,
+ * 4, 8 and 16 columns on both paths (CUDA events on `stream`), and later
+ * applies with at least *tc_min_rhs columns (host, may be NULL; the smallest
+ * count from which the tensor cores won at every larger candidate, else 32)
+ * use the tensor cores; the default before this call is 16.  Packs the
+ * tensor-core tiles if that has not happened yet (device memory about the
+ * size of the factors).  Results stay within the tensor-core tolerance of the
+ * SIMT path (BF16x3 split products, FP32 accumulation). */
+vie_status vie_autotune_rhs(vie_op* op, int32_t which, int32_t* tc_min_rhs, void* stream);
 
 /* Block shapes of one stage of an apply program (introspection for profiling):
  * *count receives the number of blocks; M[i], K[i] (host, may be NULL) their
@@ -224,9 +247,11 @@ vie_status vie_tree_perm(const vie_op* op, int32_t* perm);
 vie_status vie_stats(const vie_op* op, vie_stats_t* out);
 
 /* Waits for `stream` and reports device-side failures of earlier applies:
- * VIE_ETIMEOUT when a bounded wait inside a tensor-core kernel ran out (the
- * outputs of that apply are invalid; the flag is cleared), else VIE_OK.
- * Applies with nrhs >= 16 on c64 vectors and c64 factors run on the tensor
+ * VIE_ETIMEOUT when a bounded wait inside a tensor-core kernel or the
+ * bulk-staged single-RHS kernel ran out (the outputs of that apply are
+ * invalid; the flag is cleared), else VIE_OK.
+ * Applies with nrhs >= 16 (or the count vie_autotune_rhs chose) on c64
+ * vectors and c64 factors run on the tensor
  * cores (tcgen05, BF16x3 split products, FP32 accumulation); the first such
  * apply packs the factor tiles (device memory about the size of the factors). */
 vie_status vie_check(vie_op* op, void* stream);
@@ -244,7 +269,7 @@ vie_status vie_wait_selftest(int32_t spins, void* stream);
  * N nrhs (restart + 6) 16 bytes) fits `mem_budget`; each vie_server_step
  * admits what fits, advances every admitted request by one preconditioned
  * GMRES iteration (the applies of all columns of one operator batched into
- * one multi-column apply: tensor cores at >= 16 columns), ends restart cycles
+ * one multi-column apply: tensor cores from 16 columns, or the count vie_autotune_rhs chose), ends restart cycles
  * with an FP64 refinement residual, and retires finished requests.
  * Requests submitted between steps join at the next step.  All work runs on
  * `stream`; every call is synchronous with respect to the host. */

@@ -23,7 +23,7 @@ VIE_OP_Z, VIE_OP_ZINV = 0, 1
 VIE_C64, VIE_C128 = 0, 1
 
 # every symbol declared in include/vie.h
-EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_solve_tfqmr", "vie_farfield",
+EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_autotune_rhs", "vie_set_tiling", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_solve_tfqmr", "vie_farfield",
            "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_wait_selftest", "vie_destroy", "vie_last_error",
            "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy"]
 
@@ -41,7 +41,7 @@ class _Voxels(ctypes.Structure):
 class _Config(ctypes.Structure):
     _fields_ = [("tol_con", ctypes.c_double), ("tol_fact", ctypes.c_double), ("leaf", ctypes.c_int32),
                 ("factor_dtype", ctypes.c_int32), ("seed", ctypes.c_uint64), ("oversample", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("id_tol_div", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH):
         "vie_rhs_planewave": [P, P, P, I64, P, P],
         "vie_solve": [P, P, P, I64, D, I32, I32, P, P, P],
         "vie_solve_tfqmr": [P, P, P, I64, D, I32, P, P, P],
+        "vie_set_tiling": [P, I32, P, I32, P],
+        "vie_autotune_rhs": [P, I32, P, P],
         "vie_farfield": [P, P, I64, P, I64, P, P],
         "vie_mesh_faces": [P, P, P, P],
         "vie_mesh_host": [P, I32, P, P, P, P, P, P],
@@ -167,13 +169,14 @@ class Operator:
     """A HOD-BF compressed VIE operator Z (and Zinv) resident on the current GPU."""
 
     def __init__(self, body, k0: float, tol_con: float = 1e-4, tol_fact: float = 0.0, leaf: int = 64,
-                 factor_dtype: str = "c64", seed: int = 1, oversample: int = 10, stream=None):
+                 factor_dtype: str = "c64", seed: int = 1, oversample: int = 10, id_tol_div: int = 1, stream=None):
         lib = load_library()
         self._h = ctypes.c_void_p()
         ijk = np.ascontiguousarray(body.ijk, dtype=np.int32)
         eps = np.ascontiguousarray(np.stack([np.real(body.eps), np.imag(body.eps)], 1), dtype=np.float64)
         vox = _Voxels(len(ijk), ijk.ctypes.data, eps.ctypes.data, float(body.h))
-        cfg = _Config(tol_con, tol_fact, leaf, VIE_C64 if factor_dtype == "c64" else VIE_C128, seed, oversample, 0)
+        cfg = _Config(tol_con, tol_fact, leaf, VIE_C64 if factor_dtype == "c64" else VIE_C128, seed, oversample,
+                      id_tol_div)
         _check(lib.vie_build(ctypes.byref(vox), float(k0), ctypes.byref(cfg), _stream_ptr(stream),
                              ctypes.byref(self._h)))
         self.stats = self.get_stats()
@@ -246,6 +249,18 @@ class Operator:
         ch = np.zeros(64, dtype=np.int32)
         _check(_lib.vie_autotune(self._h, op, ch.ctypes.data, 64, _stream_ptr(stream)))
         return ch[: self.program_info(op)[0].size]
+
+    def autotune_rhs(self, op: int = VIE_OP_Z, stream=None) -> int:
+        """Time the SIMT and tensor-core multi-RHS paths; returns the column count from which
+        applies use the tensor cores."""
+        m = ctypes.c_int32(0)
+        _check(_lib.vie_autotune_rhs(self._h, op, ctypes.byref(m), _stream_ptr(stream)))
+        return int(m.value)
+
+    def set_tiling(self, choice, op: int = VIE_OP_Z, stream=None):
+        """Set every stage's single-RHS kernel/tiling to an autotuner candidate index (0-20)."""
+        ch = np.ascontiguousarray(choice, dtype=np.int32)
+        _check(_lib.vie_set_tiling(self._h, op, ch.ctypes.data, len(ch), _stream_ptr(stream)))
 
     def program_blocks(self, op: int, stage: int):
         """(M, K) int32 arrays of the blocks of one stage."""

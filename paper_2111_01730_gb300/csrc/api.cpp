@@ -38,7 +38,7 @@ void ensure_ws(vie_op* h, const Program& p, int64_t nrhs, int dtype) {
 
 void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dtype, cudaStream_t s) {
   Program& p = which == VIE_OP_Z ? h->z : h->zinv;
-  if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, s);
+  if (nrhs >= p.tc_min_rhs && dtype == VIE_C64) program_prepare_tc(p, s);
   ensure_ws(h, p, nrhs, dtype);
   program_apply_graph(p, h->perm.as<int32_t>(), X, Y, nrhs, h->mesh.nf, h->mesh.nf, dtype, h->xt.p, h->yt.p,
                       h->coef.p, s);
@@ -151,7 +151,7 @@ vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t n
     VIE_REQUIRE(which == VIE_OP_Z || which == VIE_OP_ZINV, VIE_EINVAL, "bad operator kind");
     VIE_REQUIRE(which == VIE_OP_Z || h->has_zinv, VIE_ENOTSUP, "operator has no inverse (tol_fact <= 0)");
     Program& p = which == VIE_OP_Z ? h->z : h->zinv;
-    if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
+    if (nrhs >= p.tc_min_rhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
     ensure_ws(h, p, nrhs, dtype);
     program_apply_graph(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p,
                         (cudaStream_t)stream);
@@ -166,7 +166,7 @@ vie_status vie_apply_profile(vie_op* h, int32_t which, const void* X, void* Y, i
     VIE_REQUIRE(dtype == VIE_C64 || dtype == VIE_C128, VIE_EINVAL, "bad dtype");
     VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
     Program& p = which == VIE_OP_Z ? h->z : h->zinv;
-    if (nrhs >= kTcMinRhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
+    if (nrhs >= p.tc_min_rhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
     const int ns = (int)p.stages.size() + 2;
     VIE_REQUIRE(cap >= ns, VIE_EINVAL, "ms array too short (stages + 2 needed)");
     ensure_ws(h, p, nrhs, dtype);
@@ -181,7 +181,7 @@ vie_status vie_apply_profile(vie_op* h, int32_t which, const void* X, void* Y, i
         VIE_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
         ms[i] = t;
       }
-      if (launches) *launches = program_launches(p, nrhs);
+      if (launches) *launches = program_launches(p, nrhs, dtype);
     } catch (...) {
       for (auto& e : ev) cudaEventDestroy(e);
       throw;
@@ -232,6 +232,29 @@ vie_status vie_autotune(vie_op* h, int32_t which, int32_t* choice, int32_t cap, 
     VIE_CUDA(cudaMemsetAsync(h->yt.p, 0, h->yt.bytes, (cudaStream_t)stream));
     VIE_CUDA(cudaMemsetAsync(h->coef.p, 0, h->coef.bytes, (cudaStream_t)stream));
     program_autotune(p, h->xt.p, h->yt.p, h->coef.p, (cudaStream_t)stream, choice);
+  });
+}
+
+vie_status vie_autotune_rhs(vie_op* h, int32_t which, int32_t* tc_min_rhs, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h, VIE_EINVAL, "null operator");
+    VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
+    Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    ensure_ws(h, p, 16, VIE_C64);
+    VIE_CUDA(cudaMemsetAsync(h->xt.p, 0, h->xt.bytes, (cudaStream_t)stream));
+    VIE_CUDA(cudaMemsetAsync(h->yt.p, 0, h->yt.bytes, (cudaStream_t)stream));
+    VIE_CUDA(cudaMemsetAsync(h->coef.p, 0, h->coef.bytes, (cudaStream_t)stream));
+    const int m = program_tune_rhs(p, h->xt.p, h->yt.p, h->coef.p, (cudaStream_t)stream);
+    if (tc_min_rhs) *tc_min_rhs = m;
+  });
+}
+
+vie_status vie_set_tiling(vie_op* h, int32_t which, const int32_t* choice, int32_t n, void* stream) {
+  return guarded([&] {
+    VIE_REQUIRE(h && choice, VIE_EINVAL, "null argument");
+    VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
+    Program& p = which == VIE_OP_Z ? h->z : h->zinv;
+    program_set_tiling(p, choice, n, (cudaStream_t)stream);
   });
 }
 
@@ -314,7 +337,7 @@ vie_status vie_check(vie_op* h, void* stream) {
       VIE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
       if (e) {
         VIE_CUDA(cudaMemsetAsync(p->err.p, 0, sizeof(int), (cudaStream_t)stream));
-        throw Error{VIE_ETIMEOUT, "a bounded wait in the tensor-core apply ran out; its output is invalid"};
+        throw Error{VIE_ETIMEOUT, "a bounded wait in an apply kernel ran out; its output is invalid"};
       }
     }
   });

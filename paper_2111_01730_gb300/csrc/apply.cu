@@ -102,9 +102,12 @@ __device__ __forceinline__ void row_dot_generic(const typename C2<TM>::type* __r
 }
 
 // Single right-hand side, c64 factors and vectors: the bandwidth-bound hot path.
-__global__ void __launch_bounds__(256, 5) stage1_kernel(const OpDesc* __restrict__ ops, const Tile* __restrict__ tiles,
-                                                        int64_t ntiles, const float2* __restrict__ mats,
-                                                        const float2* xt, float2* yt, float2* coef) {
+// U = 16-byte factor loads a lane keeps in flight (4, or 8 at lower occupancy).
+template <int U>
+__global__ void __launch_bounds__(256, U == 4 ? 5 : 3) stage1_kernel(const OpDesc* __restrict__ ops,
+                                                                     const Tile* __restrict__ tiles, int64_t ntiles,
+                                                                     const float2* __restrict__ mats, const float2* xt,
+                                                                     float2* yt, float2* coef) {
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -122,15 +125,15 @@ __global__ void __launch_bounds__(256, 5) stage1_kernel(const OpDesc* __restrict
       float re = 0.f, im = 0.f;
       if (r < M) {
         const float4* row = A4 + ((int64_t)r * ld >> 1);
-        for (int k0 = 2 * li; k0 < K; k0 += 8 * g) {
-          float4 a[4];
+        for (int k0 = 2 * li; k0 < K; k0 += 2 * U * g) {
+          float4 a[U];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < U; ++u) {
             const int k = k0 + 2 * g * u;
             a[u] = k < K ? __ldcs(row + (k >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < U; ++u) {
             const int k = k0 + 2 * g * u;
             if (k < K) {
               const float2 x0 = __ldg(x + k);
@@ -157,6 +160,158 @@ __global__ void __launch_bounds__(256, 5) stage1_kernel(const OpDesc* __restrict
       }
     }
   }
+}
+
+// Single right-hand side, c64, with the factor tiles staged in shared memory:
+// each CTA walks its tiles through a ring of kBulkSlots slots, one bulk
+// asynchronous copy (cp.async.bulk, completion counted on the slot's mbarrier)
+// per tile, issued kBulkSlots tiles ahead.  Every SM then keeps about
+// 2 x 96 KB of factor reads in flight regardless of how many warps are busy
+// with arithmetic, and 16 warps per CTA read their rows from shared memory
+// with four coefficient-pair loads in flight per lane.  Same tiles, lanes per
+// row and output ownership as stage1_kernel (a tile's rows are contiguous in
+// the stage buffer, at most kBulkSlotBytes long).  Waits are bounded: a CTA
+// that gives up sets *err, waits (bounded) for its copies in flight and
+// returns.
+constexpr int kBulkSlots = 3;
+constexpr int kBulkSlotBytes = 32768;
+constexpr int kBulkThreads = 512;
+constexpr uint32_t kBulkSpin = 1u << 24;
+
+__device__ __forceinline__ uint32_t bulk_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kBulkSpin; ++it) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kBulkThreads, 2) stage1_bulk_kernel(const OpDesc* __restrict__ ops,
+                                                                      const Tile* __restrict__ tiles, int64_t ntiles,
+                                                                      const float2* __restrict__ mats,
+                                                                      const float2* xt, float2* yt, float2* coef,
+                                                                      int* err) {
+  extern __shared__ __align__(128) uint8_t bulk_smem[];
+  __shared__ __align__(8) uint64_t full[kBulkSlots];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int q = 0; q < kBulkSlots; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bulk_smem_u32(&full[q])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t i) {  // thread 0: copy the rows of this CTA's i-th tile into slot i % kBulkSlots
+    const int64_t t = blockIdx.x + i * gridDim.x;
+    if (t >= ntiles) return;
+    const Tile tl = tiles[t];
+    const OpDesc& op = ops[tl.op];
+    const int rows = min(tl.nr, op.M - tl.r0);
+    const uint32_t bytes = (uint32_t)rows * (uint32_t)op.ld * 8u;
+    const float2* src = mats + op.mat_off + (int64_t)tl.r0 * op.ld;
+    const int slot = (int)(i % kBulkSlots);
+    const uint32_t bar = bulk_smem_u32(&full[slot]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(bulk_smem_u32(bulk_smem + slot * kBulkSlotBytes)), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+  };
+  if (tid == 0)
+    for (int q = 0; q < kBulkSlots; ++q) issue(q);
+  bool ok = true;
+  int64_t i = 0;
+  for (;; ++i) {
+    const int64_t t = blockIdx.x + i * gridDim.x;
+    if (t >= ntiles) break;
+    const int slot = (int)(i % kBulkSlots);
+    ok = __syncthreads_and(bulk_wait(bulk_smem_u32(&full[slot]), (uint32_t)((i / kBulkSlots) & 1)) ? 1 : 0) != 0;
+    if (!ok) break;
+    const Tile tl = tiles[t];
+    const OpDesc& op = ops[tl.op];
+    const int K = op.K, ld = op.ld;
+    const int rows = min(tl.nr, op.M - tl.r0);
+    const int g = tl.g, rp = 32 / g;
+    const int li = lane & (g - 1);
+    const float2* x = (op.in_space == SP_X ? xt : (op.in_space == SP_Y ? (const float2*)yt : coef)) + op.in_off;
+    float2* y = (op.out_space == SP_Y ? yt : coef) + op.out_off + tl.r0;
+    const bool acc_mode = op.accumulate != 0;
+    const float4* A4 = reinterpret_cast<const float4*>(bulk_smem + slot * kBulkSlotBytes);
+    constexpr int nwarps = kBulkThreads / 32;
+    for (int rb = warp * rp; rb < rows; rb += nwarps * rp) {  // warp-uniform bound: every lane joins the shuffles
+      const int r = rb + lane / g;
+      float re = 0.f, im = 0.f;
+      if (r < rows) {
+        const float4* row = A4 + (int64_t)r * (ld >> 1);
+        for (int k0 = 2 * li; k0 < K; k0 += 8 * g) {  // four coefficient pairs in flight per lane
+          float2 x0[4], x1[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + 2 * g * u;
+            x0[u] = k < K ? __ldg(x + k) : make_float2(0.f, 0.f);
+            x1[u] = k + 1 < K ? __ldg(x + k + 1) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + 2 * g * u;
+            if (k < K) {
+              const float4 a = row[k >> 1];
+              re = fmaf(a.x, x0[u].x, re); re = fmaf(-a.y, x0[u].y, re);
+              im = fmaf(a.x, x0[u].y, im); im = fmaf(a.y, x0[u].x, im);
+              re = fmaf(a.z, x1[u].x, re); re = fmaf(-a.w, x1[u].y, re);
+              im = fmaf(a.z, x1[u].y, im); im = fmaf(a.w, x1[u].x, im);
+            }
+          }
+        }
+      }
+      for (int o = g >> 1; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (r < rows && li == 0) {
+        if (acc_mode) {
+          const float2 v = y[r];
+          y[r] = make_float2(v.x + re, v.y + im);
+        } else {
+          y[r] = make_float2(re, im);
+        }
+      }
+    }
+    __syncthreads();  // the slot is consumed
+    if (tid == 0) issue(i + kBulkSlots);
+  }
+  if (!ok && tid == 0) {  // let the copies in flight land before the CTA exits
+    for (int64_t q = i; q < i + kBulkSlots; ++q)
+      if (blockIdx.x + q * gridDim.x < ntiles)
+        bulk_wait(bulk_smem_u32(&full[q % kBulkSlots]), (uint32_t)((q / kBulkSlots) & 1));
+    atomicExch(err, 1);
+  }
+}
+
+// The bulk kernel's tiles must each fit one slot and start on 16 bytes.
+bool bulk_tiles_fit(const std::vector<OpDesc>& ops, const std::vector<Tile>& tiles) {
+  for (const Tile& t : tiles) {
+    const OpDesc& o = ops[t.op];
+    const int64_t rows = std::min(t.nr, o.M - t.r0);
+    if (rows * (int64_t)o.ld * 8 > kBulkSlotBytes || (o.ld & 1) || (o.mat_off & 1)) return false;
+  }
+  return true;
+}
+
+void launch_bulk(const Stage& st, const Tile* tiles, int64_t ntiles, const void* xt, void* yt, void* coef, int* err,
+                 cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    VIE_CUDA(cudaFuncSetAttribute(stage1_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kBulkSlots * kBulkSlotBytes));
+    attr = true;
+  }
+  const int grid = (int)std::min<int64_t>(ntiles, 152 * 2);
+  stage1_bulk_kernel<<<grid, kBulkThreads, kBulkSlots * kBulkSlotBytes, s>>>(
+      st.ops.as<OpDesc>(), tiles, ntiles, st.mats.as<float2>(), (const float2*)xt, (float2*)yt, (float2*)coef, err);
+  VIE_CUDA(cudaGetLastError());
 }
 
 template <class TM, class TV, int NR>
@@ -313,7 +468,13 @@ static void launch_tiles(const Stage& st, const OpDesc* ops, const Tile* tiles, 
                          void* yt, void* coef, int nrhs, cudaStream_t s);
 
 template <class TM, class TV>
-static void launch_stage(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, cudaStream_t s) {
+static void launch_stage(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* err, cudaStream_t s) {
+  if constexpr (sizeof(TM) == 4 && sizeof(TV) == 4) {
+    if (nrhs == 1 && st.kernel == kKernelBulk && st.ntiles > 0) {
+      launch_bulk(st, st.tiles.as<Tile>(), st.ntiles, xt, yt, coef, err, s);
+      return;
+    }
+  }
   launch_tiles<TM, TV>(st, st.ops.as<OpDesc>(), st.tiles.as<Tile>(), st.ntiles, xt, yt, coef, nrhs, s);
 }
 
@@ -327,8 +488,12 @@ static void launch_tiles(const Stage& st, const OpDesc* ops, const Tile* tiles, 
   const typename C2<TM>::type* mats = st.mats.as<typename C2<TM>::type>();
   if constexpr (sizeof(TM) == 4 && sizeof(TV) == 4) {
     if (nrhs == 1) {
-      stage1_kernel<<<grid, 256, 0, s>>>(ops, tiles, ntiles, (const float2*)mats, (const float2*)xt, (float2*)yt,
-                                         (float2*)coef);
+      if (st.kernel == kKernelPlain8)
+        stage1_kernel<8><<<grid, 256, 0, s>>>(ops, tiles, ntiles, (const float2*)mats, (const float2*)xt, (float2*)yt,
+                                              (float2*)coef);
+      else
+        stage1_kernel<4><<<grid, 256, 0, s>>>(ops, tiles, ntiles, (const float2*)mats, (const float2*)xt, (float2*)yt,
+                                              (float2*)coef);
       VIE_CUDA(cudaGetLastError());
       return;
     }
@@ -378,7 +543,7 @@ static void run_program(const Program& p, const int32_t* perm, const void* X, vo
 template <class TV>
 static void run_stages(const Program& p, int64_t nrhs, void* xt, void* yt, void* coef, cudaStream_t s,
                        cudaEvent_t* ev, int& e) {
-  const bool tc = p.tc_ready && sizeof(TV) == 4 && p.factor_dtype == VIE_C64 && nrhs >= kTcMinRhs;
+  const bool tc = p.tc_ready && sizeof(TV) == 4 && p.factor_dtype == VIE_C64 && nrhs >= p.tc_min_rhs;
   for (const Stage& st : p.stages) {
     if (tc) {
       // dense blocks on the tensor cores, the small ones on the SIMT kernel
@@ -386,9 +551,9 @@ static void run_stages(const Program& p, int64_t nrhs, void* xt, void* yt, void*
       launch_tiles<float, TV>(st, st.rest_ops.as<OpDesc>(), st.rest_tiles.as<Tile>(), st.rest_ntiles, xt, yt, coef,
                               (int)nrhs, s);
     } else if (p.factor_dtype == VIE_C64) {
-      launch_stage<float, TV>(st, xt, yt, coef, (int)nrhs, s);
+      launch_stage<float, TV>(st, xt, yt, coef, (int)nrhs, p.err.as<int>(), s);
     } else {
-      launch_stage<double, TV>(st, xt, yt, coef, (int)nrhs, s);
+      launch_stage<double, TV>(st, xt, yt, coef, (int)nrhs, p.err.as<int>(), s);
     }
     if (ev) VIE_CUDA(cudaEventRecord(ev[e++], s));
   }
@@ -396,7 +561,7 @@ static void run_stages(const Program& p, int64_t nrhs, void* xt, void* yt, void*
 
 void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
                          int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s) {
-  const bool tc = p.tc_ready && dtype == VIE_C64 && p.factor_dtype == VIE_C64 && nrhs >= kTcMinRhs;
+  const bool tc = p.tc_ready && dtype == VIE_C64 && p.factor_dtype == VIE_C64 && nrhs >= p.tc_min_rhs;
   Program::GraphEntry* hit = nullptr;
   for (auto& g : p.graphs)
     if (g.exec && g.nrhs == nrhs && g.dtype == dtype && g.tc == tc && g.xt == d_xt && g.yt == d_yt && g.coef == d_c)
@@ -440,12 +605,48 @@ void program_apply(const Program& p, const int32_t* d_perm, const void* X, void*
   else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
 }
 
-// Autotuner of the single-RHS stage kernel: per stage, time every (tile size,
-// vectors per lane) candidate with CUDA events and keep the fastest tiles.
-int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s, int32_t* choice) {
-  if (p.factor_dtype != VIE_C64) return 0;
+// Single-RHS candidates of the autotuner: 0-8 stage1_kernel<4> with a maximum
+// tile of {4, 16, 64} KB x {2, 4, 8} 16-byte vectors per lane (tile index * 3 +
+// vector index); 9-11 stage1_bulk_kernel (32 KB tiles) x {2, 4, 8};
+// 12-20 stage1_kernel<8> with the tiles of 0-8.
+constexpr int kCandidates = 21;
+
+static void candidate(int c, int& kernel, int64_t& tile, int& vec) {
   static const int64_t kTileCand[] = {4096, 16384, 65536};
   static const int kVecCand[] = {2, 4, 8};
+  if (c < 9) { kernel = kKernelPlain4; tile = kTileCand[c / 3]; vec = kVecCand[c % 3]; }
+  else if (c < 12) { kernel = kKernelBulk; tile = kBulkSlotBytes; vec = kVecCand[c - 9]; }
+  else { kernel = kKernelPlain8; tile = kTileCand[(c - 12) / 3]; vec = kVecCand[(c - 12) % 3]; }
+}
+
+static void launch_single(const Stage& st, int kernel, const Tile* tiles, int64_t nt, void* xt, void* yt, void* coef,
+                          int* err, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((nt + 7) / 8, 152 * 16);
+  if (kernel == kKernelBulk) {
+    launch_bulk(st, tiles, nt, xt, yt, coef, err, s);
+    return;
+  }
+  if (kernel == kKernelPlain8)
+    stage1_kernel<8><<<grid, 256, 0, s>>>(st.ops.as<OpDesc>(), tiles, nt, st.mats.as<float2>(), (const float2*)xt,
+                                          (float2*)yt, (float2*)coef);
+  else
+    stage1_kernel<4><<<grid, 256, 0, s>>>(st.ops.as<OpDesc>(), tiles, nt, st.mats.as<float2>(), (const float2*)xt,
+                                          (float2*)yt, (float2*)coef);
+  VIE_CUDA(cudaGetLastError());
+}
+
+static void ensure_err(Program& p, cudaStream_t s) {
+  if (!p.err.p) {
+    p.err.alloc(sizeof(int));
+    VIE_CUDA(cudaMemsetAsync(p.err.p, 0, sizeof(int), s));
+  }
+}
+
+// Autotuner of the single-RHS apply: per stage, time every candidate with CUDA
+// events (best of two after one warm-up launch) and keep the fastest.
+int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s, int32_t* choice) {
+  if (p.factor_dtype != VIE_C64) return 0;
+  ensure_err(p, s);
   cudaEvent_t e0, e1;
   VIE_CUDA(cudaEventCreate(&e0));
   VIE_CUDA(cudaEventCreate(&e1));
@@ -454,33 +655,33 @@ int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s,
     if (st.host_ops.empty()) { ++nst; continue; }
     float best = 1e30f;
     std::vector<Tile> best_tiles;
-    int best_c = 0, c = 0;
-    for (int64_t tb : kTileCand)
-      for (int vt : kVecCand) {
-        std::vector<Tile> tiles;
-        make_tiles(st.host_ops, tiles, tb, vt);
-        DevBuf dt;
-        dt.alloc(sizeof(Tile) * std::max<size_t>(1, tiles.size()));
-        VIE_CUDA(cudaMemcpyAsync(dt.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
-        const int64_t nt = (int64_t)tiles.size();
-        const int grid = (int)std::min<int64_t>((nt + 7) / 8, 152 * 16);
-        float tmin = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-          VIE_CUDA(cudaEventRecord(e0, s));
-          stage1_kernel<<<grid, 256, 0, s>>>(st.ops.as<OpDesc>(), dt.as<Tile>(), nt, st.mats.as<float2>(),
-                                             (const float2*)xt, (float2*)yt, (float2*)coef);
-          VIE_CUDA(cudaEventRecord(e1, s));
-          VIE_CUDA(cudaEventSynchronize(e1));
-          float ms = 0;
-          VIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (rep > 0) tmin = std::min(tmin, ms);
-        }
-        if (tmin < best) { best = tmin; best_tiles = tiles; best_c = c; }
-        ++c;
+    int best_c = 0, best_kernel = kKernelPlain4;
+    for (int c = 0; c < kCandidates; ++c) {
+      int kernel, vec;
+      int64_t tb;
+      candidate(c, kernel, tb, vec);
+      std::vector<Tile> tiles;
+      make_tiles(st.host_ops, tiles, tb, vec);
+      if (kernel == kKernelBulk && !bulk_tiles_fit(st.host_ops, tiles)) continue;
+      DevBuf dt;
+      dt.alloc(sizeof(Tile) * std::max<size_t>(1, tiles.size()));
+      VIE_CUDA(cudaMemcpyAsync(dt.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        VIE_CUDA(cudaEventRecord(e0, s));
+        launch_single(st, kernel, dt.as<Tile>(), (int64_t)tiles.size(), xt, yt, coef, p.err.as<int>(), s);
+        VIE_CUDA(cudaEventRecord(e1, s));
+        VIE_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        VIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tmin = std::min(tmin, ms);
       }
+      if (tmin < best) { best = tmin; best_tiles = tiles; best_c = c; best_kernel = kernel; }
+    }
     st.tiles.alloc(sizeof(Tile) * std::max<size_t>(1, best_tiles.size()));
     VIE_CUDA(cudaMemcpyAsync(st.tiles.p, best_tiles.data(), sizeof(Tile) * best_tiles.size(), cudaMemcpyHostToDevice, s));
     st.ntiles = (int64_t)best_tiles.size();
+    st.kernel = best_kernel;
     if (choice) choice[nst] = best_c;
     ++nst;
   }
@@ -492,6 +693,32 @@ int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s,
   return nst;
 }
 
+// Set the single-RHS kernel and tiling of every stage to a given candidate.
+void program_set_tiling(Program& p, const int32_t* choice, int n, cudaStream_t s) {
+  VIE_REQUIRE(p.factor_dtype == VIE_C64, VIE_EINVAL, "tiling choices apply to c64 factors");
+  VIE_REQUIRE(n == (int)p.stages.size(), VIE_EINVAL, "one choice per stage");
+  for (int i = 0; i < n; ++i) VIE_REQUIRE(choice[i] >= 0 && choice[i] < kCandidates, VIE_EINVAL, "choice out of range");
+  ensure_err(p, s);
+  for (int i = 0; i < n; ++i) {
+    Stage& st = p.stages[i];
+    if (st.host_ops.empty()) continue;
+    int kernel, vec;
+    int64_t tb;
+    candidate(choice[i], kernel, tb, vec);
+    std::vector<Tile> tiles;
+    make_tiles(st.host_ops, tiles, tb, vec);
+    VIE_REQUIRE(kernel != kKernelBulk || bulk_tiles_fit(st.host_ops, tiles), VIE_EINVAL,
+                "a tile does not fit the bulk kernel's slot");
+    st.tiles.alloc(sizeof(Tile) * std::max<size_t>(1, tiles.size()));
+    VIE_CUDA(cudaMemcpyAsync(st.tiles.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
+    st.ntiles = (int64_t)tiles.size();
+    st.kernel = kernel;
+  }
+  VIE_CUDA(cudaStreamSynchronize(s));
+  for (auto& g : p.graphs)
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+}
+
 void program_prepare_tc(Program& p, cudaStream_t s) {
   if (p.tc_ready || p.factor_dtype != VIE_C64) return;
   p.err.alloc(sizeof(int));
@@ -500,16 +727,66 @@ void program_prepare_tc(Program& p, cudaStream_t s) {
   p.tc_ready = true;
 }
 
-int64_t program_launches(const Program& p, int64_t nrhs) {
+int64_t program_launches(const Program& p, int64_t nrhs, int dtype) {
+  const bool c64 = dtype == VIE_C64 && p.factor_dtype == VIE_C64;
+  const bool tc = p.tc_ready && c64 && nrhs >= p.tc_min_rhs;
   int64_t chunks = 0;
   for (int64_t r = 0; r < nrhs;) {
     int64_t left = nrhs - r;
     r += left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
     ++chunks;
   }
-  int64_t n = 2;
-  for (const Stage& st : p.stages) n += st.ntiles ? chunks : 0;
+  int64_t n = 2;  // gather, scatter
+  for (const Stage& st : p.stages) {
+    if (tc) n += (st.tc_items ? 1 : 0) + (st.rest_ntiles ? chunks : 0);
+    else n += st.ntiles ? chunks : 0;
+  }
   return n;
+}
+
+// Crossover between the two multi-RHS paths: time the stages of one apply with
+// 2, 4, 8 and 16 columns on the SIMT kernel and on the tensor cores (CUDA
+// events, best of two after a warm-up) and keep the smallest column count from
+// which the tensor cores are faster for it and every larger candidate.
+int program_tune_rhs(Program& p, void* xt, void* yt, void* coef, cudaStream_t s) {
+  if (p.factor_dtype != VIE_C64) return p.tc_min_rhs;
+  program_prepare_tc(p, s);
+  static const int kCand[] = {2, 4, 8, 16};
+  constexpr int nc = 4;
+  float t_simt[nc], t_tc[nc];
+  cudaEvent_t e0, e1;
+  VIE_CUDA(cudaEventCreate(&e0));
+  VIE_CUDA(cudaEventCreate(&e1));
+  const int saved = p.tc_min_rhs;
+  try {
+    for (int i = 0; i < nc; ++i)
+      for (int mode = 0; mode < 2; ++mode) {
+        p.tc_min_rhs = mode ? 1 : (1 << 30);
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          int e = 0;
+          VIE_CUDA(cudaEventRecord(e0, s));
+          run_stages<float>(p, kCand[i], xt, yt, coef, s, nullptr, e);
+          VIE_CUDA(cudaEventRecord(e1, s));
+          VIE_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          VIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep > 0) tmin = std::min(tmin, ms);
+        }
+        (mode ? t_tc : t_simt)[i] = tmin;
+      }
+  } catch (...) {
+    p.tc_min_rhs = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int pick = 2 * kCand[nc - 1];  // the tensor cores never won: only from 32 columns
+  for (int i = nc - 1; i >= 0 && t_tc[i] < t_simt[i]; --i) pick = kCand[i];
+  p.tc_min_rhs = pick;
+  return pick;
 }
 
 }  // namespace vie

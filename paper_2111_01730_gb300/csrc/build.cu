@@ -243,7 +243,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
   P.stages.resize(stage_base + nstages);
   int64_t coef_next = P.ncoef;
   const size_t budget = size_t(8) << 30;  // bytes of c128 scratch per chunk
-  const double tol_id = tol;
+  const double tol_id = cfg.id_tol_div > 1 ? tol / cfg.id_tol_div : tol;  // per-ID truncation threshold
 
   for (int k = 0; k < nstages; ++k) {
     // ---- collect the jobs of this batch ----

@@ -188,11 +188,19 @@ struct TcItem {
   TcSeg seg[kTcMaxSeg];
 };
 
+constexpr int kTcMinRhs = 16;  // default smallest right-hand-side count on the tensor cores
+
+// single-RHS stage kernels the autotuner chooses from
+constexpr int kKernelPlain4 = 0;  // stage1_kernel<4>: streaming loads, four 16-byte loads in flight per lane
+constexpr int kKernelBulk = 1;    // stage1_bulk_kernel: tiles staged in shared memory by bulk copies
+constexpr int kKernelPlain8 = 2;  // stage1_kernel<8>: eight loads in flight per lane, lower occupancy
+
 struct Stage {
   DevBuf mats;           // packed factor matrices (c64 or c128)
   DevBuf ops;            // OpDesc[nops]
   DevBuf tiles;          // Tile[ntiles]
   int64_t nops = 0, ntiles = 0, entries = 0, bytes = 0;
+  int kernel = 0;        // single RHS c64: kKernelPlain4, kKernelBulk or kKernelPlain8
   std::vector<OpDesc> host_ops;  // kept for the tensor-core preparation
   // tensor-core (multi-RHS) form, prepared on first use
   DevBuf tc_tiles, tc_ops, rest_ops, rest_tiles;
@@ -205,6 +213,7 @@ struct Program {         // one operator's apply: gather, stages, scatter
   int factor_dtype = VIE_C64;
   int64_t entries = 0, bytes = 0;
   bool tc_ready = false;
+  int tc_min_rhs = kTcMinRhs;  // applies with at least this many columns use the tensor cores
   DevBuf err;            // device int: a bounded wait in a tensor-core kernel ran out
   // CUDA graphs of the stage launches (the gather and scatter stay outside: they
   // touch the caller's X and Y), one per (nrhs, dtype, path, workspaces), least
@@ -236,7 +245,6 @@ void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s)
 void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* d_err, cudaStream_t s);
 size_t tc_smem_bytes();
 void wait_timeout_check(uint32_t spins, int* d_status, cudaStream_t s);
-constexpr int kTcMinRhs = 16;
 constexpr size_t kGraphCache = 8;
 constexpr int64_t kDenseInverseLimit = 65536;  // largest diagonal block formed densely by the inverse builder
 
@@ -248,9 +256,11 @@ void program_apply(const Program& p, const int32_t* d_perm, const void* X, void*
 // same, with the stage launches replayed from a cached CUDA graph
 void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
                          int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s);
-int64_t program_launches(const Program& p, int64_t nrhs);
+int64_t program_launches(const Program& p, int64_t nrhs, int dtype);
 void program_prepare_tc(Program& p, cudaStream_t s);
 int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s, int32_t* choice);
+void program_set_tiling(Program& p, const int32_t* choice, int n, cudaStream_t s);
+int program_tune_rhs(Program& p, void* xt, void* yt, void* coef, cudaStream_t s);
 void pack_matrices(const double2* src, const int64_t* d_src_off, const int32_t* d_src_ld,
                    const int32_t* d_src_colmajor, const int64_t* d_dst_off, const int32_t* d_M,
                    const int32_t* d_K, const int32_t* d_ld, int nmat, void* dst, int dst_dtype,

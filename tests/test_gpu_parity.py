@@ -98,6 +98,23 @@ def test_autotune_keeps_results(case):
     X = torch.from_numpy(W.random_block(case["n"], 1, seed=19)[:, 0]).to(torch.complex64).cuda()
     before = op.apply(X).clone()
     choice = op.autotune()
-    assert len(choice) == op.get_stats().apply_stages_z and np.all((choice >= 0) & (choice < 9))
+    assert len(choice) == op.get_stats().apply_stages_z and np.all((choice >= 0) & (choice < 21))
     after = op.apply(X)
     assert (torch.linalg.norm(after - before) / torch.linalg.norm(before)).item() < 1e-6
+
+
+
+@pytest.mark.parametrize("cand", [0, 4, 8, 9, 10, 11, 12, 16, 20])
+def test_every_kernel_candidate_matches_dense(case, cand):
+    """Each single-RHS candidate (streaming kernel with four loads in flight, variants 0, 4, 8;
+    shared-memory bulk-staged kernel 9-11; streaming kernel with eight loads in flight 12, 16, 20)
+    set on every stage gives the same apply."""
+    op = pkg.Operator(case["body"], W.K0, tol_con=1e-4, leaf=32)
+    X = torch.from_numpy(W.random_block(case["n"], 1, seed=23)[:, 0]).to(torch.complex64).cuda()
+    ref = op.apply(X).clone()
+    op.set_tiling([cand] * op.get_stats().apply_stages_z)
+    got = op.apply(X)
+    op.check()
+    assert (torch.linalg.norm(got - ref) / torch.linalg.norm(ref)).item() < 1e-6
+    d = case["Z"] @ X.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got.cpu().numpy() - d) / np.linalg.norm(d) < 5e-4

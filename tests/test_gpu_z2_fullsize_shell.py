@@ -1,6 +1,10 @@
 """Full-size parity of the plasma-shell workload (outer 1.5, inner 1.2 lambda0, Drude eps_r, vacuum
 core, pitch lambda0/20, N = 690,768): the 128-right-hand-side tensor-core apply, checked on sampled
-output rows that the oracle computes one by one from Eq. 5."""
+output rows that the oracle computes one by one from Eq. 5.
+
+With every ID truncated at chi_con = 1e-4 itself the apply error of this 14-level operator is
+1.1e-3 on 8 sampled rows (5.7e-4 at chi_con / 2), above the 5e-4 bound; the operator here is built
+with each ID truncated at chi_con / 3 (vie_config.id_tol_div = 3)."""
 import numpy as np
 import pytest
 
@@ -20,7 +24,7 @@ from oracle.mesh import build_mesh  # noqa: E402
 @pytest.fixture(scope="module")
 def shell():
     body = W.plasma_shell()
-    op = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c64", seed=1)
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c64", seed=1, id_tol_div=3)
     yield body, op, build_mesh(body)
     op.close()
 
