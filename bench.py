@@ -248,6 +248,8 @@ def run_serving(args):
     mixed = [pkg.Operator(b, W.K0, tol_con=1e-3, tol_fact=fact, leaf=64, factor_dtype="c64")
              for b, fact in zip(bodies, serving_tol_fact(bodies))]
     build_mixed = time.perf_counter() - t0
+    # where each operator's multi-column applies switch to the tensor cores (timed per operator)
+    crossover = [[m.autotune_rhs(pkg.VIE_OP_Z), m.autotune_rhs(pkg.VIE_OP_ZINV)] for m in mixed]
     rng = np.random.default_rng(7)
     nreq = args.requests
     reqs = []
@@ -310,7 +312,8 @@ def run_serving(args):
             "value": round(total_rhs / wall_s, 2), "unit": "solves/s", "higher_is_better": True,
             "config": {"workload": "; ".join(f"{b.name} (N={m.n})" for b, m in zip(bodies, fp64)),
                        "requests": nreq, "rhs_total": int(total_rhs), "rhs_per_request": "uniform 1-32",
-                       "chi_con": 1e-3, "chi_fact": "1e-1 (eps > 0), 1e-3 (eps < 0)", "restart": 30, "build_seconds": round(build_mixed, 1)},
+                       "chi_con": 1e-3, "chi_fact": "1e-1 (eps > 0), 1e-3 (eps < 0)", "restart": 30, "build_seconds": round(build_mixed, 1),
+                       "tensor_core_from_columns": {"Z": [c[0] for c in crossover], "Zinv": [c[1] for c in crossover]}},
             "saturated": {"solves_per_s": round(total_rhs / wall_s, 2), "p50_s": round(float(np.median(lat_s)), 4),
                           "p99_s": round(float(np.percentile(lat_s, 99)), 4), "max_relres": float(rel_s.max()),
                           "max_iters": int(it_s.max())},

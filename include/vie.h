@@ -263,7 +263,7 @@ vie_status vie_check(vie_op* op, void* stream);
 vie_status vie_wait_selftest(int32_t spins, void* stream);
 
 /* ---- serving: continuous batching of solves against resident operators ----
- * (spec serving loop; the paper's solver phase is Eq. 6 with Zinv.)
+ * (the paper has no serving layer; each request is the solve phase of Eq. 6 with Zinv.)
  * A server holds up to `nops` built operators (not owned).  Requests are
  * admitted while the device memory of their Krylov state (about
  * N nrhs (restart + 6) 16 bytes) fits `mem_budget`; each vie_server_step

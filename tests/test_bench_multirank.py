@@ -43,3 +43,16 @@ def test_job_value_takes_max_time_and_sums_ranks():
         v, ms = out[r]
         assert ms == pytest.approx(25.0)           # 250 ms / 10 steps on the slowest rank
         assert v == pytest.approx(2 * 1e9 / 25e-3 / 1e9)
+
+
+def test_bench_names_the_single_rhs_kernels_and_their_traffic_evidence():
+    """The roofline line names the kernels the autotuner chose and reports a DRAM-traffic ratio only
+    for a kernel whose ncu capture it comes from."""
+    import bench
+
+    names, ratio, _ = bench.single_rhs_kernels([8, 5, 5, 4])
+    assert names == "stage1_kernel<4>" and ratio == bench.TRAFFIC_RATIO
+    names, ratio, _ = bench.single_rhs_kernels([4, 10, 16])
+    assert set(names.split(" + ")) == {"stage1_kernel<4>", "stage1_bulk_kernel", "stage1_kernel<8>"}
+    assert ratio is None
+    assert bench.single_rhs_kernels([9, 11])[1] == bench.BULK_TRAFFIC_RATIO
