@@ -215,8 +215,12 @@ class HODBF:
 class HODBFInverse:
     """Algorithm 1 from its dense definition, each E_tau compressed as a butterfly."""
 
-    def __init__(self, A: np.ndarray, bounds, LH: int, tol: float):
-        """A: dense matrix in tree order (e.g. the densified compressed operator)."""
+    def __init__(self, A: np.ndarray, bounds, LH: int, tol: float, construct: str = "id"):
+        """A: dense matrix in tree order (e.g. the densified compressed operator).
+
+        construct = "id": each E_tau is compressed by IDs of its entries (Eqs. 7-10);
+        "random": by products with E_tau and E_tau^H only (BF_random_matvec of Sec. III-B),
+        each product computed from the definition E_tau X = M^-1 X - X without forming E_tau."""
         self.bounds, self.LH = bounds, LH
         lb = bounds[LH]
         self.Dinv = [np.linalg.inv(A[lb[i]:lb[i + 1], lb[i]:lb[i + 1]]) for i in range(2 ** LH)]
@@ -231,10 +235,18 @@ class HODBFInverse:
                 M = np.eye(b - a, dtype=np.complex128)
                 M[:m - a, m - a:] = B1
                 M[m - a:, :m - a] = B2
-                E = np.linalg.inv(M) - np.eye(b - a)
                 L = LH - l
                 ob = sub_bounds(bounds, l, i, L)
-                self.E[(l, i)] = Butterfly(lambda r, c, E=E, a=a: E[np.ix_(r - a, c - a)], ob, ob, L, tol)
+                if construct == "random":
+                    from .bf_random import RandomButterfly
+
+                    lu = sla.lu_factor(M)
+                    mv = lambda X, lu=lu: sla.lu_solve(lu, X) - X  # noqa: E731
+                    rmv = lambda Y, lu=lu: sla.lu_solve(lu, Y, trans=2) - Y  # noqa: E731
+                    self.E[(l, i)] = RandomButterfly(mv, rmv, ob, ob, L, tol, seed=l * 1000 + i)
+                else:
+                    E = np.linalg.inv(M) - np.eye(b - a)
+                    self.E[(l, i)] = Butterfly(lambda r, c, E=E, a=a: E[np.ix_(r - a, c - a)], ob, ob, L, tol)
 
     def apply(self, x: np.ndarray) -> np.ndarray:
         b = self.bounds

@@ -79,3 +79,56 @@ def test_inverse_quality(tree_Z, tol_fact, bound):
     x = W.random_block(len(Zt), 2, seed=5)
     err = np.linalg.norm(Hi.apply(Hd @ x) - x) / np.linalg.norm(x)
     assert err <= bound
+
+
+# ---- butterflies from products only (BF_random_matvec of Sec. III-B) ----------------
+
+from oracle.bf_random import RandomButterfly  # noqa: E402
+from oracle.hodbf import Butterfly, sub_bounds  # noqa: E402
+
+
+def _level1_block(tree_Z):
+    Zt, bounds, LH = tree_Z
+    L = LH - 1
+    ob, sb = sub_bounds(bounds, 1, 0, L), sub_bounds(bounds, 1, 1, L)
+    return Zt[ob[0][0]:ob[0][-1], sb[0][0]:sb[0][-1]], ob, sb, L
+
+
+def test_random_butterfly_exact_on_low_rank_block(tree_Z):
+    """A rank-6 block is reproduced to rounding: every sketch sees the whole range."""
+    _, ob, sb, L = _level1_block(tree_Z)
+    rng = np.random.default_rng(2)
+    m, n = ob[0][-1] - ob[0][0], sb[0][-1] - sb[0][0]
+    A = (rng.standard_normal((m, 6)) + 1j * rng.standard_normal((m, 6))) @ (
+        rng.standard_normal((6, n)) + 1j * rng.standard_normal((6, n)))
+    rb = RandomButterfly(lambda X: A @ X, lambda Y: A.conj().T @ Y, ob, sb, L, 1e-12)
+    x = W.random_block(n, 2, seed=3)
+    assert np.linalg.norm(rb.apply(x) - A @ x) < 1e-10 * np.linalg.norm(A @ x)
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-5])
+def test_random_butterfly_accuracy_and_product_count(tree_Z, tol):
+    """On a VIE off-diagonal block: error within 10 tol like the ID butterfly, storage of the same
+    order, and no more product columns than the two half-depth sweeps need."""
+    A, ob, sb, L = _level1_block(tree_Z)
+    rb = RandomButterfly(lambda X: A @ X, lambda Y: A.conj().T @ Y, ob, sb, L, tol, p=8)
+    x = W.random_block(A.shape[1], 2, seed=4)
+    assert np.linalg.norm(rb.apply(x) - A @ x) <= 10 * tol * np.linalg.norm(A @ x)
+    bf = Butterfly(lambda r, c: A[np.ix_(r - ob[0][0], c - sb[0][0])], ob, sb, L, tol)
+    assert rb.entries() <= 2 * bf.entries()
+    h = L // 2
+    widest = int(max(np.diff(ob[L]).max(), np.diff(sb[L]).max()))  # largest leaf of either tree
+    rmax = max([v.shape[0] for v in rb.V] + [u.shape[0] for Ut in rb.U for Ui in Ut for u in Ui])
+    assert rb.products <= (2 ** (h + 1) + 2 ** (L - h + 1)) * (max(rmax, widest) + 8)
+
+
+@pytest.mark.parametrize("tol_fact,bound", [(1e-1, 0.5), (1e-3, 1e-2)])
+def test_inverse_from_products_quality(tree_Z, tol_fact, bound):
+    """Algorithm 1 with every E_tau built from products with E_tau and E_tau^H only."""
+    Zt, bounds, LH = tree_Z
+    H = HODBF(lambda r, c: Zt[np.ix_(r, c)], bounds, LH, 1e-4)
+    Hd = H.dense()
+    Hi = HODBFInverse(Hd, bounds, LH, tol_fact, construct="random")
+    x = W.random_block(len(Zt), 2, seed=5)
+    err = np.linalg.norm(Hi.apply(Hd @ x) - x) / np.linalg.norm(x)
+    assert err <= bound
