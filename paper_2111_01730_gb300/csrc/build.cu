@@ -345,6 +345,20 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
       std::vector<int32_t> srcs(nj);
       for (int q = 0; q < nj; ++q)  // leaf blocks carry their leaf index as the source
         srcs[q] = jobs[q0 + q].bf >= 0 ? bfs[jobs[q0 + q].bf].src : (int32_t)jobs[q0 + q].blk;
+      {  // row node of every ID job (for sources that sketch instead of sampling rows)
+        std::vector<int64_t> lo(nj, -1), hi(nj, -1);
+        for (int q = 0; q < nj; ++q) {
+          const Job& j = jobs[q0 + q];
+          if (!j.id) continue;
+          const BF& B = bfs[j.bf];
+          const int64_t nnu = int64_t(1) << (B.L - j.k);
+          const int tlev = B.l + j.k;
+          const int64_t tidx = B.i * (int64_t(1) << j.k) + j.blk / nnu;
+          lo[q] = t.bounds[tlev][tidx];
+          hi[q] = t.bounds[tlev][tidx + 1];
+        }
+        src.set_row_ranges(lo, hi);
+      }
       const auto te0 = std::chrono::steady_clock::now();
       src.eval(eb, prefix, rows, cols, srcs, aoff, dA.as<double2>(), s);
       VIE_CUDA(cudaStreamSynchronize(s));

@@ -276,6 +276,10 @@ struct BuildResult {
 // Where the builder takes matrix entries from (tree positions in, c128 col-major blocks out).
 struct EntrySource {
   virtual ~EntrySource() = default;
+  // Row ranges [row_lo[q], row_hi[q]) of the row node of each job of the next eval (ID jobs
+  // only; -1 for the others).  A source may return, for an ID job whose m rows are a sample
+  // of that range, m other rows with the same column geometry (e.g. a Gaussian sketch).
+  virtual void set_row_ranges(const std::vector<int64_t>& /*row_lo*/, const std::vector<int64_t>& /*row_hi*/) {}
   virtual void eval(const std::vector<EntryBlock>& eb, const std::vector<int64_t>& prefix,
                     const std::vector<int32_t>& rows, const std::vector<int32_t>& cols,
                     const std::vector<int32_t>& srcs, int64_t total, double2* dA, cudaStream_t s) = 0;

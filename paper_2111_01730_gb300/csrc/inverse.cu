@@ -12,22 +12,34 @@
 // (the same matrix as above), with D_tau = Z(tau, tau) from the entry
 // evaluator: an LU factorization of D_tau and a two-sided triangular solve
 // with diag(D_tau1, D_tau2) as right-hand sides (two n x n matrices per node).
-// It is then compressed by the same ID-based butterfly construction as Z
-// (Eqs. 7-10), reading its entries from the dense matrix.  This replaces the
-// randomized recompression (BF_random_matvec inside BF_SMW, Algorithm 2) and
+// It is then compressed by the same level-by-level ID construction as Z
+// (Eqs. 7-10), except that each ID reads a Gaussian row sketch G^H E_tau(tau', :)
+// of its row node tau' (products of E_tau^H with random vectors supported on
+// tau', as the randomized construction of Sec. III-B does) instead of sampled
+// rows; the B^L blocks read exact entries.  This replaces the randomized
+// recompression from black-box products (BF_random_matvec inside BF_SMW,
+// Algorithm 2) and
 // is limited by the dense blocks: a level joins the inverse when its largest
 // node fits twice in the free device memory and holds at most
 // kDenseInverseLimit unknowns; above the first level that does not, the
 // inverse is block diagonal.  Nodes of a level are compressed in batches
 // whose dense E_tau fit in memory together.
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <chrono>
+#include <map>
+#include <tuple>
 
 #include "internal.h"
 
 namespace vie {
 
+#define VIE_CUBLAS(call)                                                                      \
+  do {                                                                                        \
+    cublasStatus_t st_ = (call);                                                              \
+    if (st_ != CUBLAS_STATUS_SUCCESS) throw Error{VIE_ECUDA, std::string(#call) + " failed"}; \
+  } while (0)
 #define VIE_CUSOLVER(call)                                                                      \
   do {                                                                                          \
     cusolverStatus_t st_ = (call);                                                              \
@@ -77,8 +89,53 @@ __global__ void gather_dense(const DenseRef* mats, const EntryBlock* blocks, con
 
 int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
+// Complex Gaussian entries (unit variance) from a counter-based hash: splitmix64 of
+// (seed, index) gives two uniforms, the Box-Muller transform two normals.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_fill(float2* g, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t h = mix64(seed ^ mix64((uint64_t)i));
+    const float u1 = ((uint32_t)(h >> 40) + 1u) * (1.0f / 16777217.0f);  // (0, 1]
+    const float u2 = (uint32_t)(h & 0xFFFFFFu) * (1.0f / 16777216.0f);
+    const float r = sqrtf(-logf(u1));  // |z|^2 / 2 of a unit complex normal
+    float sn, cs;
+    sincosf(6.28318530717958647692f * u2, &sn, &cs);
+    g[i] = make_float2(r * cs, r * sn);
+  }
+}
+
+struct SketchJob {
+  int64_t out_off, col_off;  // block output offset, first column in the column pool
+  int32_t m, n;              // sketch rows used, columns
+  int64_t s_off;             // the group's sketch S (K x ld, column-major)
+  int32_t K, pad;
+  int64_t base;              // tree position of column 0 of S
+};
+
+// dA[out_off + i + c m] = S[i + (col_c - base) K] for every sketched ID job
+__global__ void sketch_gather(const SketchJob* jobs, int nj, const int32_t* cols, const float2* S, double2* dA) {
+  const SketchJob j = jobs[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < (int64_t)j.m * j.n; e += blockDim.x) {
+    const int i = int(e % j.m), c = int(e / j.m);
+    const float2 v = S[j.s_off + i + (int64_t)(cols[j.col_off + c] - j.base) * j.K];
+    dA[j.out_off + e] = make_double2(v.x, v.y);
+  }
+}
+
 struct DenseSource : EntrySource {
   std::vector<DenseRef> refs;
+  std::vector<int64_t> lo, hi;  // row node of each ID job of the next eval
+  bool sketch = false;          // ID jobs read G^H E(tau, :) instead of sampled rows of E
+  uint64_t seed = 1;
+  cublasHandle_t blas = nullptr;
+  ~DenseSource() override { if (blas) cublasDestroy(blas); }
+  void set_row_ranges(const std::vector<int64_t>& l, const std::vector<int64_t>& h) override { lo = l; hi = h; }
   void eval(const std::vector<EntryBlock>& eb, const std::vector<int64_t>& prefix, const std::vector<int32_t>& rows,
             const std::vector<int32_t>& cols, const std::vector<int32_t>& srcs, int64_t total, double2* dA,
             cudaStream_t s) override {
@@ -101,7 +158,51 @@ struct DenseSource : EntrySource {
                                                    dsrc.as<int32_t>(), nj, total, drows.as<int32_t>(),
                                                    dcols.as<int32_t>(), dA);
     VIE_CUDA(cudaGetLastError());
+    if (sketch) sketch_jobs(eb, cols, srcs, dA, s);
     VIE_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ID jobs whose rows are a sample of their row node tau get, in place of those m rows,
+  // the first m rows of S = G^H E(tau, :), G a complex Gaussian |tau| x K block (K the
+  // largest m of the jobs sharing tau): products of E^H with random vectors supported on
+  // tau, the row sketch the randomized construction uses (Sec. III-B).
+  void sketch_jobs(const std::vector<EntryBlock>& eb, const std::vector<int32_t>& cols,
+                   const std::vector<int32_t>& srcs, double2* dA, cudaStream_t s) {
+    if (lo.size() != eb.size()) return;
+    std::map<std::tuple<int32_t, int64_t, int64_t>, std::vector<int>> groups;
+    for (int q = 0; q < (int)eb.size(); ++q)
+      if (lo[q] >= 0 && eb[q].m < hi[q] - lo[q]) groups[{srcs[q], lo[q], hi[q]}].push_back(q);
+    if (groups.empty()) return;
+    if (!blas) VIE_CUBLAS(cublasCreate(&blas));
+    VIE_CUBLAS(cublasSetStream(blas, s));
+    DevBuf dcols;
+    dcols.alloc(sizeof(int32_t) * std::max<size_t>(1, cols.size()));
+    VIE_CUDA(cudaMemcpyAsync(dcols.p, cols.data(), sizeof(int32_t) * cols.size(), cudaMemcpyHostToDevice, s));
+    for (auto& kv : groups) {
+      const DenseRef& R = refs[std::get<0>(kv.first)];
+      const int64_t a = std::get<1>(kv.first), b = std::get<2>(kv.first), rows = b - a, n = R.ld;
+      int K = 0;
+      for (int q : kv.second) K = std::max(K, eb[q].m);
+      DevBuf G, S, dj;
+      G.alloc(sizeof(float2) * rows * K);
+      S.alloc(sizeof(float2) * (int64_t)K * n);
+      const uint64_t gseed = seed ^ ((uint64_t)std::get<0>(kv.first) << 48) ^ ((uint64_t)a << 24) ^ (uint64_t)b;
+      gaussian_fill<<<grid_for(rows * K), 256, 0, s>>>(G.as<float2>(), rows * K, gseed);
+      VIE_CUDA(cudaGetLastError());
+      const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+      // S (K x n) = G^H (K x rows) E(a:b, :) (rows x n); E column-major with ld = n
+      VIE_CUBLAS(cublasCgemm(blas, CUBLAS_OP_C, CUBLAS_OP_N, K, (int)n, (int)rows, &one, (const cuComplex*)G.p,
+                             (int)rows, (const cuComplex*)(R.p + (a - R.base)), (int)n, &zero, (cuComplex*)S.p, K));
+      std::vector<SketchJob> js;
+      for (int q : kv.second)
+        js.push_back(SketchJob{eb[q].out_off, eb[q].col_off, eb[q].m, eb[q].n, 0, K, 0, R.base});  // s_off 0: one S
+      dj.alloc(sizeof(SketchJob) * js.size());
+      VIE_CUDA(cudaMemcpyAsync(dj.p, js.data(), sizeof(SketchJob) * js.size(), cudaMemcpyHostToDevice, s));
+      sketch_gather<<<(int)js.size(), 256, 0, s>>>(dj.as<SketchJob>(), (int)js.size(), dcols.as<int32_t>(),
+                                                   S.as<float2>(), dA);
+      VIE_CUDA(cudaGetLastError());
+      VIE_CUDA(cudaStreamSynchronize(s));  // G, S, dj are released at the end of this iteration
+    }
   }
 };
 
@@ -212,6 +313,8 @@ void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
     for (int64_t i0 = 0; i0 < nn;) {
       std::vector<DevBuf> E;
       DenseSource src;
+      src.sketch = true;  // IDs of E_tau from Gaussian row sketches (products with E_tau^H)
+      src.seed = h->cfg.seed ^ (0x5851F42D4C957F2Dull * (uint64_t)(l + 1));
       std::vector<BfSpec> specs;
       int64_t used = 0;
       int64_t i = i0;

@@ -78,8 +78,8 @@ def test_five_layer_sphere_tfqmr_rcs_vs_multilayer_mie():
           "RCS relative RMSE", rmse)
     assert st == pkg.VIE_OK
     # the paper reports 2 TFQMR iterations at chi_fact 1e-1 for its layered sphere; the inverse
-    # built here (sampled-row IDs of the dense E_tau, complex FP32) needs about 20
-    assert st_.zinv_top_level == 0 and it[0] <= 30
+    # built here (sketched IDs of the dense E_tau, complex FP32) needs about 10
+    assert st_.zinv_top_level == 0 and it[0] <= 15
     assert max(rmse) < 0.05
 
 
@@ -102,5 +102,5 @@ def test_two_shell_sphere_tfqmr_rcs_vs_multilayer_mie():
         rmse.append(np.sqrt(np.mean((g - m) ** 2)) / m.max())
     print("two-shell sphere: zinv top level", op.get_stats().zinv_top_level, "TFQMR iterations", it[0],
           "relres", rel[0], "RCS relative RMSE", rmse)
-    assert st == pkg.VIE_OK and it[0] <= 30
+    assert st == pkg.VIE_OK and it[0] <= 15      # the paper: 7 for its two-shell sphere
     assert max(rmse) < 0.05
