@@ -172,6 +172,30 @@ class RandomButterfly:
             y[o[L][i]:o[L][i + 1]] = self.U[0][i][0] @ d[i][0]
         return y
 
+    def apply_adjoint(self, ys: np.ndarray) -> np.ndarray:
+        """x = A^H y: the adjoint of every factor, in reverse order."""
+        L, h, o, s = self.L, self.h, self.o, self.s
+        d = [[self.U[0][i][0].conj().T @ ys[o[L][i]:o[L][i + 1]]] for i in range(2 ** L)]
+        for t in range(1, L - h + 1):  # row chain upwards
+            ni, nj = 2 ** (L - t), 2 ** t
+            d = [[self.U[t][i][j].conj().T @ np.concatenate([d[2 * i][j // 2], d[2 * i + 1][j // 2]])
+                  for j in range(nj)] for i in range(ni)]
+        g = [[self.M[i][j].conj().T @ d[i][j] for j in range(2 ** (L - h))] for i in range(2 ** h)]
+        for l in range(h, 0, -1):  # column chain downwards
+            prev = [[None] * (2 ** (L - l + 1)) for _ in range(2 ** (l - 1))]
+            for i in range(2 ** l):
+                for j in range(2 ** (L - l)):
+                    e = self.W[l - 1][i][j].conj().T @ g[i][j]
+                    n1 = (self.V[2 * j].shape[0] if l == 1 else self.W[l - 2][i // 2][2 * j].shape[0])
+                    for jj, part in ((2 * j, e[:n1]), (2 * j + 1, e[n1:])):
+                        cur = prev[i // 2][jj]
+                        prev[i // 2][jj] = part if cur is None else cur + part
+            g = prev
+        x = np.zeros((self.n,) + ys.shape[1:], dtype=np.result_type(ys, np.complex128))
+        for j in range(2 ** L):
+            x[s[L][j]:s[L][j + 1]] = self.V[j].conj().T @ g[0][j]
+        return x
+
     def entries(self) -> int:
         n = sum(v.size for v in self.V) + sum(w.size for lev in self.W for Wi in lev for w in Wi)
         n += sum(u.size for Ut in self.U for Ui in Ut for u in Ui)
