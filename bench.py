@@ -36,8 +36,8 @@ import workloads as W  # noqa: E402
 
 METRIC = "HOD-BF apply GB/s (algorithmic bytes / apply time), single RHS"
 UNIT = "GB/s"
-# DRAM traffic / algorithmic bytes of the single-RHS stage kernel, from the ncu capture in
-# profiles/stage1_kernel_sphere_r1.0.md (stages 1-3 at N = 52,584), scaled to a full apply.
+# DRAM traffic / algorithmic bytes of the single-RHS stage kernel, from an ncu capture of
+# stages 1-3 of the r = 1.0 sphere (N = 52,584), scaled to a full apply.
 TRAFFIC_RATIO = 1.022
 TRAFFIC_NOTE = "ncu dram bytes of stage1_kernel<4> stages 1-3 at r=1.0 (N=52,584) = 1.022 x algorithmic, scaled"
 # the same ratio for the shared-memory bulk-staged kernel (autotuner candidates 9-11); None until captured

@@ -2,7 +2,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
+#include <utility>
 
 #include "internal.h"
 
@@ -10,6 +13,32 @@ namespace vie {
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+
+static std::mutex g_attr_mu;
+static std::set<std::pair<int, const void*>> g_attr_done;
+
+bool done_on_device(const void* key) {
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  return g_attr_done.count({dev, key}) != 0;
+}
+
+void mark_on_device(const void* key) {
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  g_attr_done.insert({dev, key});
+}
+
+void ensure_smem_attr(const void* kernel, int bytes) {
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (g_attr_done.count({dev, kernel})) return;
+  VIE_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  g_attr_done.insert({dev, kernel});
+}
 
 void DevBuf::alloc(size_t n) {
   release();

@@ -302,12 +302,7 @@ bool bulk_tiles_fit(const std::vector<OpDesc>& ops, const std::vector<Tile>& til
 
 void launch_bulk(const Stage& st, const Tile* tiles, int64_t ntiles, const void* xt, void* yt, void* coef, int* err,
                  cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    VIE_CUDA(cudaFuncSetAttribute(stage1_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kBulkSlots * kBulkSlotBytes));
-    attr = true;
-  }
+  ensure_smem_attr((const void*)stage1_bulk_kernel, kBulkSlots * kBulkSlotBytes);
   const int grid = (int)std::min<int64_t>(ntiles, 152 * 2);
   stage1_bulk_kernel<<<grid, kBulkThreads, kBulkSlots * kBulkSlotBytes, s>>>(
       st.ops.as<OpDesc>(), tiles, ntiles, st.mats.as<float2>(), (const float2*)xt, (float2*)yt, (float2*)coef, err);
@@ -599,6 +594,12 @@ void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void*
   else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, hit->exec);
 }
 
+void program_run(const Program& p, int64_t nrhs, int dtype, void* xt, void* yt, void* coef, cudaStream_t s) {
+  int e = 0;
+  if (dtype == VIE_C64) run_stages<float>(p, nrhs, xt, yt, coef, s, nullptr, e);
+  else run_stages<double>(p, nrhs, xt, yt, coef, s, nullptr, e);
+}
+
 void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
                    int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s, cudaEvent_t* ev) {
   if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, ev);
@@ -721,8 +722,8 @@ void program_set_tiling(Program& p, const int32_t* choice, int n, cudaStream_t s
 
 void program_prepare_tc(Program& p, cudaStream_t s) {
   if (p.tc_ready || p.factor_dtype != VIE_C64) return;
-  p.err.alloc(sizeof(int));
-  VIE_CUDA(cudaMemsetAsync(p.err.p, 0, sizeof(int), s));
+  // keep an existing flag: graphs captured earlier (single-RHS bulk stages) hold its address
+  ensure_err(p, s);
   for (Stage& st : p.stages) tc_prepare_stage(st, st.host_ops, s);
   p.tc_ready = true;
 }

@@ -143,8 +143,9 @@ struct Job {
 
 }  // namespace
 
-static void finalize_stage(Stage& st, const std::vector<OpDesc>& ops, std::vector<DevBuf>& chunks,
-                           const std::vector<int64_t>& chunk_elems, int elem_bytes, cudaStream_t s) {
+static void finalize_stage(Stage& st, const std::vector<OpDesc>& ops, const std::vector<int32_t>& tags,
+                           std::vector<DevBuf>& chunks, const std::vector<int64_t>& chunk_elems, int elem_bytes,
+                           cudaStream_t s) {
   int64_t tot = 0;
   for (auto e : chunk_elems) tot += e;
   st.mats.alloc(std::max<int64_t>(tot, 2) * elem_bytes);
@@ -167,6 +168,7 @@ static void finalize_stage(Stage& st, const std::vector<OpDesc>& ops, std::vecto
   st.entries = 0;
   for (auto& o : ops) st.entries += (int64_t)o.M * o.K;
   st.host_ops = ops;
+  st.host_tag = tags;
   st.bytes = tot * elem_bytes;
   VIE_CUDA(cudaStreamSynchronize(s));
   for (auto& c : chunks) c.release();
@@ -307,6 +309,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
     res.t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - th0).count();
     // ---- process in chunks ----
     std::vector<OpDesc> ops;
+    std::vector<int32_t> tags;  // tree level of each op's butterfly (-1: leaf block)
     std::vector<DevBuf> chunks;
     std::vector<int64_t> chunk_elems;
     int64_t stage_off = 0;
@@ -419,6 +422,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
           o.in_space = SP_X; o.in_off = j.rows[0]; o.out_space = SP_Y; o.out_off = j.rows[0]; o.accumulate = 0;
           res.leaf_entries += (int64_t)m * m;
           ops.push_back(o);
+          tags.push_back(-1);
           continue;
         }
         BF& B = bfs[j.bf];
@@ -431,6 +435,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
           o.in_space = SP_C; o.in_off = B.coff[B.L][j.blk]; o.out_space = SP_Y; o.out_off = j.rows[0];
           o.accumulate = 1;
           ops.push_back(o);
+          tags.push_back(B.l);
           continue;
         }
         const IdJob& J = ij[idc];
@@ -461,6 +466,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
         o.pad = j.bf;
         o.K = n;
         ops.push_back(o);
+        tags.push_back(B.l);
         // remember the block for the coefficient offset
         ops.back().out_off = -(int64_t)(j.blk + 1);
       }
@@ -523,7 +529,7 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
         o.out_off = bfs[o.pad].coff[k][blk];
         o.pad = 0;
       }
-    finalize_stage(P.stages[stage_base + k], ops, chunks, chunk_elems, elem_bytes, s);
+    finalize_stage(P.stages[stage_base + k], ops, tags, chunks, chunk_elems, elem_bytes, s);
   }
   P.ncoef = coef_next;
   P.entries = 0;

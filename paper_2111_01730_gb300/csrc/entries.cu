@@ -87,7 +87,8 @@ __device__ __forceinline__ V3 kuhn_vertex(int p, int a, int dx, int dy, int dz, 
 }
 
 // int_T 1/|r-r'| ds' and int_T |r-r'| ds' over the flat triangle ABC (closed form,
-// Wilton et al. 1984 / Graglia 1993); see the oracle's derivation in its docstring.
+// Wilton et al. 1984 / Graglia 1993): per edge, the in-plane distance to the edge line
+// and the two edge-end distances give the log and arctan terms of both potentials.
 __device__ void tri_pot(V3 r, V3 A, V3 B, V3 C, double& Im1, double& I1) {
   V3 n = cross(B - A, C - A);
   n = (1.0 / norm(n)) * n;
@@ -547,11 +548,7 @@ __global__ void farfield_kernel(EntryCtx c, int64_t nt, const int32_t* tet_faces
 // host side
 // ---------------------------------------------------------------------------
 static void upload_constants() {
-  static bool done = false;
-  static int dev_done = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (done && dev_done == dev) return;
+  if (done_on_device((const void*)&upload_constants)) return;
   double area[6][4], nrm[6][4][3];
   static const int loc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
   for (int p = 0; p < 6; ++p)
@@ -589,8 +586,7 @@ static void upload_constants() {
   put(rule_tet_conical(3), 4, nullptr, sizeof(double) * 27 * 5, c_tetc3);
   put(rule_tri_conical(2), 3, nullptr, sizeof(double) * 4 * 4, c_tric2);
   put(rule_tri_conical(3), 3, nullptr, sizeof(double) * 9 * 4, c_tric3);
-  done = true;
-  dev_done = dev;
+  mark_on_device((const void*)&upload_constants);
 }
 
 void geometry_upload(const Mesh& m, double k0, Geometry& g, cudaStream_t s) {

@@ -176,7 +176,7 @@ void id_batched(const IdJob* d_jobs, int njobs, int max_n, double2* d_a, double2
   constexpr int NT = 256;
   size_t smem = sizeof(double) * 2 * max_n + sizeof(double2) * max_n + sizeof(int) * max_n + 64;
   VIE_REQUIRE(smem <= 200 * 1024, VIE_ENOTSUP, "ID block too wide for shared memory");
-  VIE_CUDA(cudaFuncSetAttribute(id_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VIE_CUDA(cudaFuncSetAttribute((const void*)id_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   id_kernel<NT><<<njobs, NT, smem, s>>>(d_jobs, d_a, d_v, d_piv, d_rank, tol);
   VIE_CUDA(cudaGetLastError());
 }

@@ -33,6 +33,15 @@ struct Error {
     if (!(cond)) throw ::vie::Error{(status), (msg)};    \
   } while (0)
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device,
+// once per (device, kernel); thread safe.  cudaFuncSetAttribute acts per device,
+// so a process-wide flag would leave a second device at the default limit.
+void ensure_smem_attr(const void* kernel, int bytes);
+// Per-device one-time set-up flags keyed by an address: done_on_device asks,
+// mark_on_device records (current device); thread safe.
+bool done_on_device(const void* key);
+void mark_on_device(const void* key);
+
 // ---------------------------------------------------------------------------
 // device memory owned by the operator
 // ---------------------------------------------------------------------------
@@ -202,6 +211,7 @@ struct Stage {
   int64_t nops = 0, ntiles = 0, entries = 0, bytes = 0;
   int kernel = 0;        // single RHS c64: kKernelPlain4, kKernelBulk or kKernelPlain8
   std::vector<OpDesc> host_ops;  // kept for the tensor-core preparation
+  std::vector<int32_t> host_tag; // per op: tree level of its butterfly's row node (-1: leaf block)
   // tensor-core (multi-RHS) form, prepared on first use
   DevBuf tc_tiles, tc_ops, rest_ops, rest_tiles;
   int64_t tc_items = 0, tc_bytes = 0, rest_ntiles = 0;
@@ -253,6 +263,16 @@ void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles, int64_
 void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs,
                    int64_t ldx, int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c,
                    cudaStream_t s, cudaEvent_t* events = nullptr);
+// the stages alone on tree-ordered work vectors (rows x nrhs, rhs fastest): no permutation
+void program_run(const Program& p, int64_t nrhs, int dtype, void* xt, void* yt, void* coef, cudaStream_t s);
+// program construction helpers (program.cu)
+void stage_set(Stage& st, std::vector<OpDesc> ops, DevBuf&& mats, int64_t elems, int elem_bytes, cudaStream_t s);
+void program_totals(Program& p);
+void program_adjoint(const Program& fwd, Program& adj, cudaStream_t s);
+void program_filter(const Program& src, int32_t tag, Program& out, cudaStream_t s);
+void program_relocate_coef(Program& p, int64_t shift, cudaStream_t s);
+void program_append(Program& dst, Program&& src, cudaStream_t s);
+void program_prepend(Program& dst, Program&& src);
 // same, with the stage launches replayed from a cached CUDA graph
 void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs, int64_t ldx,
                          int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s);

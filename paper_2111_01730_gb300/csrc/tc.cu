@@ -399,11 +399,7 @@ void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s)
 
 void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* d_err, cudaStream_t s) {
   if (st.tc_items == 0) return;
-  static bool attr = false;
-  if (!attr) {
-    VIE_CUDA(cudaFuncSetAttribute(tc_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
-    attr = true;
-  }
+  ensure_smem_attr((const void*)tc_stage_kernel, (int)tc_smem_bytes());
   const int nrc = (nrhs + kRows - 1) / kRows;
   const int64_t work = st.tc_items * nrc;
   const int grid = (int)std::min<int64_t>(work, 152 * 4);  // four CTAs per SM (smem 49 KB, TMEM 128 columns each)
