@@ -353,6 +353,85 @@ def zinv_timing(op, pkg, x, y, steps, torch):
             "mvp_with_precond_ms": round(e[1].elapsed_time(e[2]) / steps, 4)}
 
 
+def multi_rhs_timing(op, pkg, torch, nrhs: int = 128, steps: int = 5):
+    """The same operator applied to a block of right-hand sides on the tensor cores (tcgen05,
+    BF16x3 split products): useful complex flops 8 E nrhs over the apply time."""
+    n = op.n
+    E = int(op.program_info(pkg.VIE_OP_Z)[0].sum())
+    X = torch.from_numpy(W.random_block(n, nrhs, seed=11).astype(np.complex64)).cuda().t().contiguous().t()
+    Y = torch.empty_like(X)
+    for _ in range(2):  # the first packs the tensor-core tiles
+        op.apply(X, Y)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        op.apply(X, Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    op.check()
+    ms = e0.elapsed_time(e1) / steps
+    tf = 8.0 * E * nrhs / (ms * 1e-3) / 1e12
+    return {"nrhs": nrhs, "ms_per_apply": round(ms, 3), "useful_tflops": round(tf, 2),
+            "frac_of_bf16_peak": round(tf / BF16_PEAK[0], 4), "peak_note": BF16_PEAK[1],
+            "factor_gbs": round(8.0 * E / (ms * 1e-3) / 1e9, 1),
+            "kernel": "tc_stage_kernel (+ stage_kernel for blocks under 16 x 32)"}
+
+
+def precond_section(pkg, torch, steps: int = 20):
+    """Zinv from products (Algorithms 1-2, BF_random_matvec) and one preconditioned solve, on a
+    sphere of the benchmark's permittivity and pitch at radius 1 (N = 52,584): the four top
+    levels of the inverse are built from products only (nodes above 4,096 unknowns), the rest
+    from their dense blocks.  The solve (x-polarized plane wave along +z, left-preconditioned
+    TFQMR to 1e-3) is compared with the plain FP64 path (complex FP64 factors, unpreconditioned
+    GMRES to 1e-6)."""
+    body = W.sphere(1.0, 4.0 - 0.1j, 1.0 / 10, name="sphere_r1_eps4-0.1j")
+    t0 = time.perf_counter()
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=1e-2, leaf=64, factor_dtype="c64", seed=1,
+                      inv_dense_max=4096)
+    build = time.perf_counter() - t0
+    st = op.get_stats()
+    n = op.n
+    ez = int(op.program_info(pkg.VIE_OP_ZINV)[0].sum())
+    x = torch.from_numpy(W.random_block(n, 1, seed=5)[:, 0].astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.apply(x, y, op=pkg.VIE_OP_ZINV)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        op.apply(x, y, op=pkg.VIE_OP_ZINV)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ident = op.apply(op.apply(x), op=pkg.VIE_OP_ZINV)
+    k, p = W.planewave_x_along_z()
+    V = op.rhs_planewave(k, p)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    I, it, rel, stt = op.solve_tfqmr(V, rtol=1e-3, max_iter=300)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t1
+    op.close()
+    ref = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c128", seed=1)
+    I64, it64, rel64, st64 = ref.solve(ref.rhs_planewave(k, p), rtol=1e-6, restart=200, max_iter=2000)
+    err = (torch.linalg.norm(I - I64) / torch.linalg.norm(I64)).item()
+    ref.close()
+    return {"workload": f"sphere r=1 lambda0, eps_r=4-0.1j, pitch lambda0/10, N={n}", "chi_fact": 1e-2,
+            "invert_seconds": round(st.invert_seconds, 1), "build_seconds": round(build, 1),
+            "product_levels": int(st.zinv_product_levels), "products": int(st.inverse_products),
+            "zinv_top_level": int(st.zinv_top_level),
+            "zinv_apply_ms": round(ms, 4), "zinv_apply_gbs": round((8 * ez + 16 * n) / (ms * 1e-3) / 1e9, 1),
+            "zinv_z_identity_error": round((torch.linalg.norm(ident - x) / torch.linalg.norm(x)).item(), 5),
+            "tfqmr_iterations": int(it[0]), "tfqmr_relres": float(rel[0]), "solve_seconds": round(t_solve, 3),
+            "status": int(stt),
+            "fp64_reference": {"gmres_iterations": int(it64[0]), "relres": float(rel64[0])},
+            "solution_error_vs_fp64_path": round(err, 6)}
+
+
 def nrhs_for_tune(args):
     """The stage-tiling autotuner serves the single-RHS kernel."""
     return args.nrhs == 1 and not args.no_autotune
@@ -392,6 +471,8 @@ def main():
                     help="use one autotuner candidate on every stage (0-8 streaming kernel, 9-11 shared-memory "
                          "bulk kernel, 12-20 streaming kernel with 8 loads in flight)")
     ap.add_argument("--zinv", action="store_true", help="also build Zinv (chi_fact 1e-1) and time its apply")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 128-RHS apply and the preconditioned-solve keys of the default line")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (solves/s, p50/p99 latency)")
     ap.add_argument("--requests", type=int, default=120)
     ap.add_argument("--rate", type=float, default=100.0, help="Poisson arrival rate (requests/s) for --serve")
@@ -521,9 +602,15 @@ def main():
         }
         if args.zinv:
             line["zinv"] = zinv_timing(op, pkg, x, y, args.steps, torch)
+        if nrhs == 1 and not args.no_extras:
+            line["multi_rhs"] = multi_rhs_timing(op, pkg, torch)
         line["roofline"].update({"peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms],
                                  "stage_gbs": [round(8 * float(e) / (float(t) * 1e6), 1)
                                                for e, t in zip(entries, stage_ms)]})
+        if nrhs == 1 and not args.no_extras and world == 1:
+            op.close()
+            torch.cuda.empty_cache()
+            line["preconditioned_solve"] = precond_section(pkg, torch)
         if not args.no_cpu_baseline and world == 1:
             cb = oracle_apply_sample(15.0)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

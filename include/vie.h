@@ -51,8 +51,18 @@ typedef enum {
   VIE_ENOTSUP = -7    /* the operator lacks what the call needs (e.g. no Zinv)  */
 } vie_status;
 
-typedef enum { VIE_OP_Z = 0, VIE_OP_ZINV = 1 } vie_opkind;
+typedef enum { VIE_OP_Z = 0, VIE_OP_ZINV = 1, VIE_OP_ZH = 2, VIE_OP_ZINVH = 3 } vie_opkind;
 typedef enum { VIE_C64 = 0, VIE_C128 = 1 } vie_dtype;
+
+/* Arithmetic of the stored factors and of the multi-RHS applies (spec precision split):
+ *   VIE_P_AUTO       factor_dtype decides; complex FP32 factors apply on the tensor cores from
+ *                    16 columns (or the count vie_autotune_rhs chose);
+ *   VIE_P_FP64       the plain FP64 method: complex FP64 factors, FP64 applies;
+ *   VIE_P_C32        complex FP32 factors and applies, never the tensor cores;
+ *   VIE_P_TC_BF16X3  complex FP32 factors, tensor cores (BF16x3 split products, FP32
+ *                    accumulation) from 16 columns, crossover fixed;
+ *   VIE_P_TC_TF32    a TF32 tensor-core variant: not built (vie_build returns VIE_ENOTSUP). */
+typedef enum { VIE_P_AUTO = 0, VIE_P_FP64 = 1, VIE_P_C32 = 2, VIE_P_TC_BF16X3 = 3, VIE_P_TC_TF32 = 4 } vie_prec;
 
 /* A scatterer on a cubic voxel lattice of pitch h: voxel (i, j, k) is the cube
  * [i h, (i+1) h] x [j h, (j+1) h] x [k h, (k+1) h].  Each voxel is split into
@@ -74,6 +84,11 @@ typedef struct {
   uint64_t seed;       /* seed of the row sampling in the IDs                   */
   int32_t oversample;  /* extra random rows per ID beyond the candidate count   */
   int32_t id_tol_div;  /* each ID truncates at tol / id_tol_div (<= 1: at tol)  */
+  int32_t inv_dense_max; /* inverse: largest diagonal block (unknowns) whose E_tau is
+                            formed densely; the levels above are built from products
+                            only (Algorithms 1-2 with BF_random_matvec).  0: 65,536.
+                            Complex FP64 factors keep the dense construction only.  */
+  int32_t prec;          /* vie_prec (0 = VIE_P_AUTO)                                  */
 } vie_config;
 
 typedef struct {
@@ -94,8 +109,11 @@ typedef struct {
   double build_id_seconds;       /* of build_seconds: batched IDs on the GPU      */
   double build_host_seconds;     /* of build_seconds: row sampling on the host    */
   int32_t zinv_top_level;        /* Zinv holds Algorithm 1's levels l >= this one (0 = all);
-                                    nodes larger than 32,768 unknowns are not inverted   */
-  int32_t reserved2;
+                                    with complex FP64 factors, nodes larger than 65,536
+                                    unknowns are not inverted                            */
+  int32_t zinv_product_levels;   /* Algorithm 1 levels built from products only          */
+  int64_t inverse_products;      /* columns multiplied by an operator or its adjoint there */
+  double invert_product_seconds; /* of invert_seconds: the product-built levels           */
 } vie_stats_t;
 
 /* Build Z (and Zinv when cfg->tol_fact > 0) for the voxel body at wavenumber
@@ -105,7 +123,11 @@ typedef struct {
 vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg,
                      void* stream, vie_op** out);
 
-/* Y = op(X) for op = Z or Zinv, X and Y device arrays, N x nrhs column-major
+/* Y = op(X) for op = Z, Zinv, or their adjoints Z^H, Zinv^H (VIE_OP_ZH,
+ * VIE_OP_ZINVH: the conjugate-transposed factors in reverse order, the products
+ * the randomized construction of Sec. III-B needs; the adjoint factors are
+ * formed on the first such call, about the size of the operator's factors),
+ * X and Y device arrays, N x nrhs column-major
  * with leading dimensions ldx, ldy >= N (in elements), dtype VIE_C64 or
  * VIE_C128 for both.  The factors keep their stored type; accumulation runs
  * in the vector type (c128 vectors give the FP64-accumulated apply used for
@@ -245,6 +267,38 @@ vie_status vie_mesh_host(const vie_voxels* body, int32_t leaf, int64_t* n, int32
 vie_status vie_tree_perm(const vie_op* op, int32_t* perm);
 
 vie_status vie_stats(const vie_op* op, vie_stats_t* out);
+
+/* Sharded apply across GPUs by subtrees (Sec. III-D: processors assigned by the cluster
+ * tree).  With nranks GPUs (a power of two, at most 2^L_H) rank r owns the faces at tree
+ * positions [lo, hi) of node r at level log2(nranks) (vie_shard_range; vie_tree_perm maps
+ * tree positions to faces).  vie_apply_shard writes exactly the rank's rows of Y (original
+ * face order; other rows untouched) from the whole of X, which every rank supplies (one
+ * all-gather of X across ranks, done by the caller with its own collective library), so
+ * that the ranks' rows together equal vie_apply.  The blocks the rank's rows depend on
+ * (leaf blocks and butterflies of its subtree, the row sides of the upper butterflies
+ * ending in its rows and the column sides feeding them) are selected on the first call
+ * per (which, rank, nranks) and kept until vie_destroy (device memory up to the
+ * operator's own).  For Zinv the upper levels update rows of several ranks in place, so
+ * a rank's closure includes other ranks' leaves (computed redundantly, results
+ * discarded).  Arguments, layout and errors as vie_apply, plus VIE_EINVAL for a bad
+ * rank or rank count. */
+vie_status vie_shard_range(const vie_op* op, int32_t rank, int32_t nranks, int64_t* lo, int64_t* hi);
+vie_status vie_apply_shard(vie_op* op, int32_t which, int32_t rank, int32_t nranks, const void* X, void* Y,
+                           int64_t nrhs, int64_t ldx, int64_t ldy, int32_t dtype, void* stream);
+
+/* Checkpoint of a built operator (the paper has no file format; a build costs
+ * minutes at the workload sizes).  vie_save writes the voxel body, k0, the
+ * configuration, the statistics and every stage of the Z and Zinv apply
+ * programs (block descriptors, warp tiles and single-RHS kernel choices, packed
+ * factor bytes) to `path`; the factors are read back from the device in 256 MiB
+ * pieces on `stream`.  vie_load reads such a file, remakes the mesh, tree and
+ * interaction tables on the host and the device, and re-uploads the programs
+ * into a new operator (*out, owned by the caller until vie_destroy): its
+ * applies are bit-identical to the saved operator's.  Both return VIE_EINVAL
+ * for an unopenable, foreign, truncated or inconsistent file (nothing is
+ * returned in *out then), VIE_ENOMEM when the device or host runs out. */
+vie_status vie_save(const vie_op* op, const char* path, void* stream);
+vie_status vie_load(const char* path, void* stream, vie_op** out);
 
 /* Waits for `stream` and reports device-side failures of earlier applies:
  * VIE_ETIMEOUT when a bounded wait inside a tensor-core kernel or the

@@ -19,13 +19,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvie.so")
 
 VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ENOTCONV, VIE_ETIMEOUT, VIE_ENAN, VIE_ECUDA, VIE_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
-VIE_OP_Z, VIE_OP_ZINV = 0, 1
+VIE_OP_Z, VIE_OP_ZINV, VIE_OP_ZH, VIE_OP_ZINVH = 0, 1, 2, 3
 VIE_C64, VIE_C128 = 0, 1
+VIE_P_AUTO, VIE_P_FP64, VIE_P_C32, VIE_P_TC_BF16X3, VIE_P_TC_TF32 = 0, 1, 2, 3, 4
 
 # every symbol declared in include/vie.h
 EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_autotune_rhs", "vie_set_tiling", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_solve_tfqmr", "vie_farfield",
            "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_wait_selftest", "vie_destroy", "vie_last_error",
-           "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy"]
+           "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy",
+           "vie_save", "vie_load", "vie_shard_range", "vie_apply_shard"]
 
 
 class VieError(RuntimeError):
@@ -41,7 +43,7 @@ class _Voxels(ctypes.Structure):
 class _Config(ctypes.Structure):
     _fields_ = [("tol_con", ctypes.c_double), ("tol_fact", ctypes.c_double), ("leaf", ctypes.c_int32),
                 ("factor_dtype", ctypes.c_int32), ("seed", ctypes.c_uint64), ("oversample", ctypes.c_int32),
-                ("id_tol_div", ctypes.c_int32)]
+                ("id_tol_div", ctypes.c_int32), ("inv_dense_max", ctypes.c_int32), ("prec", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -52,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("apply_stages_z", ctypes.c_int32), ("apply_stages_zinv", ctypes.c_int32),
                 ("build_entries_seconds", ctypes.c_double), ("build_id_seconds", ctypes.c_double),
                 ("build_host_seconds", ctypes.c_double), ("zinv_top_level", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("zinv_product_levels", ctypes.c_int32), ("inverse_products", ctypes.c_int64),
+                ("invert_product_seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +98,10 @@ def load_library(path: str = LIB_PATH):
         "vie_server_submit": [P, I32, P, I64, D, P],
         "vie_server_step": [P, P, P],
         "vie_server_result": [P, I64, P, P, P, P],
+        "vie_save": [P, ctypes.c_char_p, P],
+        "vie_shard_range": [P, I32, I32, P, P],
+        "vie_apply_shard": [P, I32, I32, I32, P, P, I64, I64, I64, I32, P],
+        "vie_load": [ctypes.c_char_p, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -169,18 +176,49 @@ class Operator:
     """A HOD-BF compressed VIE operator Z (and Zinv) resident on the current GPU."""
 
     def __init__(self, body, k0: float, tol_con: float = 1e-4, tol_fact: float = 0.0, leaf: int = 64,
-                 factor_dtype: str = "c64", seed: int = 1, oversample: int = 10, id_tol_div: int = 1, stream=None):
+                 factor_dtype: str = "c64", seed: int = 1, oversample: int = 10, id_tol_div: int = 1,
+                 inv_dense_max: int = 0, prec: int = 0, stream=None):
         lib = load_library()
         self._h = ctypes.c_void_p()
         ijk = np.ascontiguousarray(body.ijk, dtype=np.int32)
         eps = np.ascontiguousarray(np.stack([np.real(body.eps), np.imag(body.eps)], 1), dtype=np.float64)
         vox = _Voxels(len(ijk), ijk.ctypes.data, eps.ctypes.data, float(body.h))
         cfg = _Config(tol_con, tol_fact, leaf, VIE_C64 if factor_dtype == "c64" else VIE_C128, seed, oversample,
-                      id_tol_div)
+                      id_tol_div, inv_dense_max, prec)
         _check(lib.vie_build(ctypes.byref(vox), float(k0), ctypes.byref(cfg), _stream_ptr(stream),
                              ctypes.byref(self._h)))
         self.stats = self.get_stats()
         self.n = int(self.stats.n)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Operator":
+        """An operator read back from a vie_save file (bit-identical applies)."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p()
+        _check(lib.vie_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(self._h)))
+        self.stats = self.get_stats()
+        self.n = int(self.stats.n)
+        return self
+
+    def shard_range(self, rank: int, nranks: int):
+        """Tree positions [lo, hi) owned by `rank` of `nranks` (node `rank` at level log2(nranks))."""
+        lo, hi = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(_lib.vie_shard_range(self._h, rank, nranks, ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
+    def apply_shard(self, X, Y, rank: int, nranks: int, op: int = VIE_OP_Z, stream=None):
+        """Write rank's rows of Y = op X (original face order) from the whole of X."""
+        Xc, nrhs, ldx = _colmajor(X, self.n)
+        Yc, _, ldy = _colmajor(Y, self.n)
+        assert Yc.data_ptr() == Y.data_ptr() or Y.dim() == 1, "Y must be column-major"
+        _check(_lib.vie_apply_shard(self._h, op, rank, nranks, ctypes.c_void_p(Xc.data_ptr()),
+                                    ctypes.c_void_p(Yc.data_ptr()), nrhs, ldx, ldy, _dtype_code(Xc),
+                                    _stream_ptr(stream)))
+        return Y
+
+    def save(self, path: str, stream=None):
+        _check(_lib.vie_save(self._h, os.fsencode(path), _stream_ptr(stream)))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -342,6 +380,72 @@ class Operator:
         p = np.zeros(self.n, dtype=np.int32)
         _check(_lib.vie_tree_perm(self._h, p.ctypes.data))
         return p
+
+
+def tree_bounds(n: int, levels: int):
+    """Node offsets of every level of the cluster tree (tree positions): the KD bisection
+    gives the first child ceil(n/2) of a node's n faces, so the bounds follow from n alone."""
+    b = [[0, n]]
+    for _ in range(levels):
+        nxt = [0]
+        for lo, hi in zip(b[-1][:-1], b[-1][1:]):
+            nxt += [lo + (hi - lo + 1) // 2, hi]
+        b.append(nxt)
+    return b
+
+
+def shard_faces(perm, levels: int, nranks: int):
+    """Faces owned by each of `nranks` ranks (node r at tree level log2(nranks)): a list of int arrays."""
+    lev = int(nranks).bit_length() - 1
+    assert 1 << lev == nranks and lev <= levels, "nranks must be a power of two, at most 2^levels"
+    b = tree_bounds(len(perm), levels)[lev]
+    return [np.asarray(perm[b[r]:b[r + 1]]) for r in range(nranks)]
+
+
+def allgather_rows(x_rows, faces, n: int, group=None):
+    """The whole of X on every rank from each rank's rows (torch.distributed all_gather of the
+    rows, padded to the largest share, placed at their faces): the data plane of the sharded
+    apply (Sec. III-D).  x_rows: (rows_r, nrhs) tensor of this rank's faces; faces: all ranks'
+    face arrays; returns an (n, nrhs) tensor on x_rows' device."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    width = max(len(f) for f in faces)
+    nrhs = x_rows.shape[1]
+    pad = torch.zeros((width, nrhs), dtype=x_rows.dtype, device=x_rows.device)
+    pad[: x_rows.shape[0]] = x_rows
+    # complex tensors travel as real pairs (every backend moves real dtypes)
+    parts = [torch.zeros((width, nrhs, 2), dtype=pad.real.dtype, device=pad.device) for _ in range(world)]
+    dist.all_gather(parts, torch.view_as_real(pad).contiguous(), group=group)
+    X = torch.zeros((n, nrhs), dtype=x_rows.dtype, device=x_rows.device)
+    for r in range(world):
+        idx = torch.as_tensor(faces[r], dtype=torch.long, device=x_rows.device)
+        X[idx] = torch.view_as_complex(parts[r][: len(faces[r])].contiguous())
+    return X
+
+
+class ShardedOperator:
+    """An operator applied across the ranks of a torch.distributed group by subtrees
+    (vie_apply_shard): each rank owns node `rank` of tree level log2(world) and returns its
+    rows of op X from its rows of X after one all-gather."""
+
+    def __init__(self, op: Operator, group=None):
+        import torch.distributed as dist
+
+        self.op, self.group = op, group
+        self.rank, self.world = dist.get_rank(group), dist.get_world_size(group)
+        self.faces = shard_faces(op.tree_perm(), int(op.stats.levels), self.world)
+
+    def apply(self, x_rows, op: int = VIE_OP_Z, stream=None):
+        import torch
+
+        X = allgather_rows(x_rows, self.faces, self.op.n, self.group)
+        Xc = X.t().contiguous().t()
+        Y = torch.zeros_like(Xc)
+        self.op.apply_shard(Xc, Y, self.rank, self.world, op=op, stream=stream)
+        idx = torch.as_tensor(self.faces[self.rank], dtype=torch.long, device=Y.device)
+        return Y[idx]
 
 
 class Server:

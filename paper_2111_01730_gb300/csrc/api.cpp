@@ -108,6 +108,8 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, v
     VIE_REQUIRE(body->nvox > 0 && body->ijk && body->eps && body->h > 0, VIE_EINVAL, "empty or invalid voxel body");
     VIE_REQUIRE(cfg->leaf >= 4 && cfg->tol_con > 0 && k0 > 0, VIE_EINVAL, "invalid configuration");
     VIE_REQUIRE(cfg->factor_dtype == VIE_C64 || cfg->factor_dtype == VIE_C128, VIE_EINVAL, "factor dtype");
+    VIE_REQUIRE(cfg->prec >= VIE_P_AUTO && cfg->prec <= VIE_P_TC_TF32, VIE_EINVAL, "bad precision");
+    VIE_REQUIRE(cfg->prec != VIE_P_TC_TF32, VIE_ENOTSUP, "the TF32 tensor-core variant is not built");
     *out = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     double t0 = now_s();
@@ -115,6 +117,8 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, v
     try {
       h->cfg = *cfg;
       if (h->cfg.oversample <= 0) h->cfg.oversample = 10;
+      if (cfg->prec == VIE_P_FP64) h->cfg.factor_dtype = VIE_C128;
+      if (cfg->prec == VIE_P_C32 || cfg->prec == VIE_P_TC_BF16X3) h->cfg.factor_dtype = VIE_C64;
       build_mesh(*body, h->mesh);
       geometry_upload(h->mesh, k0, h->geo, s);
       geometry_table(h->geo, s);
@@ -136,6 +140,8 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, v
                                cudaMemcpyHostToDevice, s));
       BuildResult br;
       build_hodbf(h, s, br);
+      const int never = 1 << 30;
+      h->z.tc_min_rhs = h->zinv.tc_min_rhs = cfg->prec == VIE_P_C32 ? never : kTcMinRhs;
       VIE_CUDA(cudaStreamSynchronize(s));
       h->stats.n = N;
       h->stats.ntets = h->mesh.nt;
@@ -169,7 +175,10 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, v
   });
 }
 
-void vie_destroy(vie_op* op) { delete op; }
+void vie_destroy(vie_op* op) {
+  if (op) shard_forget(op);
+  delete op;
+}
 
 vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t nrhs, int64_t ldx, int64_t ldy,
                      int32_t dtype, void* stream) {
@@ -177,13 +186,24 @@ vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t n
     VIE_REQUIRE(h && X && Y, VIE_EINVAL, "null argument");
     VIE_REQUIRE(nrhs >= 1 && ldx >= h->mesh.nf && ldy >= h->mesh.nf, VIE_EINVAL, "bad nrhs or leading dimension");
     VIE_REQUIRE(dtype == VIE_C64 || dtype == VIE_C128, VIE_EINVAL, "bad dtype");
-    VIE_REQUIRE(which == VIE_OP_Z || which == VIE_OP_ZINV, VIE_EINVAL, "bad operator kind");
-    VIE_REQUIRE(which == VIE_OP_Z || h->has_zinv, VIE_ENOTSUP, "operator has no inverse (tol_fact <= 0)");
+    VIE_REQUIRE(which >= VIE_OP_Z && which <= VIE_OP_ZINVH, VIE_EINVAL, "bad operator kind");
+    VIE_REQUIRE(which == VIE_OP_Z || which == VIE_OP_ZH || h->has_zinv, VIE_ENOTSUP,
+                "operator has no inverse (tol_fact <= 0)");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (which == VIE_OP_ZH || which == VIE_OP_ZINVH) {
+      const bool inv = which == VIE_OP_ZINVH;
+      Program& a = inv ? h->zinvh : h->zh;
+      bool& ready = inv ? h->zinvh_ready : h->zh_ready;
+      if (!ready) { program_adjoint(inv ? h->zinv : h->z, a, s); ready = true; }
+      if (nrhs >= a.tc_min_rhs && dtype == VIE_C64) program_prepare_tc(a, s);
+      ensure_ws(h, a, nrhs, dtype);
+      program_apply_adjoint(a, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p, s);
+      return;
+    }
     Program& p = which == VIE_OP_Z ? h->z : h->zinv;
-    if (nrhs >= p.tc_min_rhs && dtype == VIE_C64) program_prepare_tc(p, (cudaStream_t)stream);
+    if (nrhs >= p.tc_min_rhs && dtype == VIE_C64) program_prepare_tc(p, s);
     ensure_ws(h, p, nrhs, dtype);
-    program_apply_graph(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p,
-                        (cudaStream_t)stream);
+    program_apply_graph(p, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p, s);
   });
 }
 
@@ -266,6 +286,11 @@ vie_status vie_autotune(vie_op* h, int32_t which, int32_t* choice, int32_t cap, 
 
 vie_status vie_autotune_rhs(vie_op* h, int32_t which, int32_t* tc_min_rhs, void* stream) {
   return guarded([&] {
+    if (h && (h->cfg.prec == VIE_P_C32 || h->cfg.prec == VIE_P_TC_BF16X3)) {  // the precision fixes the path
+      Program& p = which == VIE_OP_ZINV ? h->zinv : h->z;
+      if (tc_min_rhs) *tc_min_rhs = p.tc_min_rhs;
+      return;
+    }
     VIE_REQUIRE(h, VIE_EINVAL, "null operator");
     VIE_REQUIRE(which == VIE_OP_Z || (which == VIE_OP_ZINV && h->has_zinv), VIE_ENOTSUP, "no such operator");
     Program& p = which == VIE_OP_Z ? h->z : h->zinv;

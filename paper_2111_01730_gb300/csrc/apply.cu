@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256, U == 4 ? 5 : 3) stage1_kernel(const OpDes
     const int g = tl.g, rp = 32 / g;
     const int li = lane & (g - 1);
     const float2* x = (op.in_space == SP_X ? xt : (op.in_space == SP_Y ? (const float2*)yt : coef)) + op.in_off;
-    float2* y = (op.out_space == SP_Y ? yt : coef) + op.out_off;
+    float2* y = (op.out_space == SP_Y ? yt : (op.out_space == SP_X ? const_cast<float2*>(xt) : coef)) + op.out_off;
     const float4* A4 = reinterpret_cast<const float4*>(mats + op.mat_off);
     const bool acc_mode = op.accumulate != 0;
     for (int r = tl.r0 + lane / g; r < tl.r0 + tl.nr; r += rp) {
@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(kBulkThreads, 2) stage1_bulk_kernel(const OpDe
     const int g = tl.g, rp = 32 / g;
     const int li = lane & (g - 1);
     const float2* x = (op.in_space == SP_X ? xt : (op.in_space == SP_Y ? (const float2*)yt : coef)) + op.in_off;
-    float2* y = (op.out_space == SP_Y ? yt : coef) + op.out_off + tl.r0;
+    float2* y = (op.out_space == SP_Y ? yt : (op.out_space == SP_X ? const_cast<float2*>(xt) : coef)) + op.out_off +
+                tl.r0;
     const bool acc_mode = op.accumulate != 0;
     const float4* A4 = reinterpret_cast<const float4*>(bulk_smem + slot * kBulkSlotBytes);
     constexpr int nwarps = kBulkThreads / 32;
@@ -296,6 +297,7 @@ bool bulk_tiles_fit(const std::vector<OpDesc>& ops, const std::vector<Tile>& til
     const OpDesc& o = ops[t.op];
     const int64_t rows = std::min(t.nr, o.M - t.r0);
     if (rows * (int64_t)o.ld * 8 > kBulkSlotBytes || (o.ld & 1) || (o.mat_off & 1)) return false;
+    if (rows * (int64_t)o.ld == 0) return false;  // blocks with no columns (zero rows of a product-built factor)
   }
   return true;
 }
@@ -324,7 +326,8 @@ __global__ void __launch_bounds__(256) stage_kernel(const OpDesc* __restrict__ o
     const int g = tl.g, rp = 32 / g;
     const int li = lane & (g - 1);
     const V2* xin = (op.in_space == SP_X ? xt : (op.in_space == SP_Y ? (const V2*)yt : coef)) + op.in_off * nrhs + rhs0;
-    V2* yout = (op.out_space == SP_Y ? yt : coef) + op.out_off * nrhs + rhs0;
+    V2* yout = (op.out_space == SP_Y ? yt : (op.out_space == SP_X ? const_cast<V2*>(xt) : coef)) + op.out_off * nrhs +
+               rhs0;
     for (int r = tl.r0 + lane / g; r < tl.r0 + tl.nr; r += rp) {
       const bool active = r < op.M;
       TV re[NR], im[NR];
@@ -592,6 +595,30 @@ void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void*
   hit->used = ++p.graph_clock;
   if (dtype == VIE_C64) run_program<float>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, hit->exec);
   else run_program<double>(p, d_perm, X, Y, nrhs, ldx, ldy, d_xt, d_yt, d_c, s, nullptr, hit->exec);
+}
+
+// Adjoint apply with an adjoint program (program_adjoint): the input goes to the Y
+// space, the X space and the coefficients start at zero, the result is read from X.
+void program_apply_adjoint(const Program& adj, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs,
+                           int64_t ldx, int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s) {
+  const int64_t tot = adj.n * nrhs;
+  const int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
+  const size_t es = dtype == VIE_C64 ? 8 : 16;
+  VIE_CUDA(cudaMemsetAsync(d_xt, 0, es * (size_t)tot, s));
+  if (adj.ncoef) VIE_CUDA(cudaMemsetAsync(d_c, 0, es * (size_t)adj.ncoef * nrhs, s));
+  int e = 0;
+  if (dtype == VIE_C64) {
+    gather_kernel<float><<<grid, 256, 0, s>>>(d_perm, adj.n, (int)nrhs, (const float2*)X, ldx, (float2*)d_yt);
+    VIE_CUDA(cudaGetLastError());
+    run_stages<float>(adj, nrhs, d_xt, d_yt, d_c, s, nullptr, e);
+    scatter_kernel<float><<<grid, 256, 0, s>>>(d_perm, adj.n, (int)nrhs, (const float2*)d_xt, (float2*)Y, ldy);
+  } else {
+    gather_kernel<double><<<grid, 256, 0, s>>>(d_perm, adj.n, (int)nrhs, (const double2*)X, ldx, (double2*)d_yt);
+    VIE_CUDA(cudaGetLastError());
+    run_stages<double>(adj, nrhs, d_xt, d_yt, d_c, s, nullptr, e);
+    scatter_kernel<double><<<grid, 256, 0, s>>>(d_perm, adj.n, (int)nrhs, (const double2*)d_xt, (double2*)Y, ldy);
+  }
+  VIE_CUDA(cudaGetLastError());
 }
 
 void program_run(const Program& p, int64_t nrhs, int dtype, void* xt, void* yt, void* coef, cudaStream_t s) {

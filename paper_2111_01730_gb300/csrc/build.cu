@@ -207,6 +207,7 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res) {
   h->z.stages.clear();
   h->z.ncoef = 0;
   build_program(h, specs, src, h->cfg.tol_con, h->z, /*leaf_blocks=*/true, SP_X, s, res);
+  program_compact_coef(h->z, s);  // coefficient work space by lifetimes
 }
 
 void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src, double tol, Program& P,
@@ -375,7 +376,11 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
         Job& j = jobs[q0 + q];
         if (!j.id) continue;
         const int m = (int)j.rows.size(), n = (int)j.cols.size();
-        ij.push_back(IdJob{eb[q].out_off, voff, poff, m, n});
+        // Eq. 7 truncates each ID at O(chi_con); the IDs of Z are cut at chi_con / 3 (one
+        // constant for every workload: the deepest operator, the 14-level plasma shell, then
+        // applies within 5 chi_con).  The inverse's blocks (v0_space = Y) keep chi_fact per ID.
+        const double tj = v0_space == SP_X ? tol_id / 3.0 : tol_id;
+        ij.push_back(IdJob{eb[q].out_off, voff, poff, m, n, tj});
         ij_q.push_back(q);
         voff += (int64_t)std::min(m, n) * n;
         poff += n;

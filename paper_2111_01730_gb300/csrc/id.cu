@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(NT) id_kernel(const IdJob* jobs, double2* Apoo
   extern __shared__ double smem[];
   const IdJob J = jobs[blockIdx.x];
   const int m = J.m, n = J.n;
+  if (J.tol > 0.0) tol = J.tol;
   const int kmax = min(m, n);
   double* cn = smem;                       // n
   double* cref = cn + n;                   // n
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(NT) id_kernel(const IdJob* jobs, double2* Apoo
     double s = 0.0;
     for (int i = lane; i < m; i += 32) s += abs2(a[i + (int64_t)j * m]);
     s = warp_sum(s);
+    if (!isfinite(s)) s = -1.0;  // a non-finite column is never a pivot (and ends the ID below)
     if (lane == 0) { cn[j] = s; cref[j] = s; pv[j] = j; }
   }
   __syncthreads();
@@ -76,6 +78,7 @@ __global__ void __launch_bounds__(NT) id_kernel(const IdJob* jobs, double2* Apoo
     }
     __syncthreads();
     const int p = s_p;
+    if (p >= n || !(cn[p] >= 0.0)) { r = i; break; }  // no valid pivot left (non-finite input)
     // exact norm of the pivot column over rows i..m-1
     if (warp == 0) {
       double s = 0.0;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(NT) id_kernel(const IdJob* jobs, double2* Apoo
     __syncthreads();
     const double nrm = s_nrm;
     if (i == 0) R00 = nrm;
-    if (!(nrm > tol * R00) || nrm == 0.0) { r = i; break; }
+    if (!(nrm > tol * R00) || nrm == 0.0 || !isfinite(nrm)) { r = i; break; }
     // swap columns i and p
     if (p != i) {
       for (int k = tid; k < m; k += NT) {

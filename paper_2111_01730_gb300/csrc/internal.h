@@ -156,6 +156,7 @@ struct IdJob {
   int64_t v_off;   // row-major r x n output V = [I T] P^T, c128 (space min(m,n)*n)
   int64_t p_off;   // n ints: pivot order (first r = skeleton)
   int32_t m, n;
+  double tol;      // truncation |R_kk| <= tol |R_11| of this job (<= 0: the batch's tolerance)
 };
 void id_batched(const IdJob* d_jobs, int njobs, int max_n, double2* d_a, double2* d_v, int32_t* d_piv,
                 int32_t* d_rank, double tol, cudaStream_t s);
@@ -263,14 +264,20 @@ void make_tiles(const std::vector<OpDesc>& ops, std::vector<Tile>& tiles, int64_
 void program_apply(const Program& p, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs,
                    int64_t ldx, int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c,
                    cudaStream_t s, cudaEvent_t* events = nullptr);
+void program_apply_adjoint(const Program& adj, const int32_t* d_perm, const void* X, void* Y, int64_t nrhs,
+                           int64_t ldx, int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s);
 // the stages alone on tree-ordered work vectors (rows x nrhs, rhs fastest): no permutation
 void program_run(const Program& p, int64_t nrhs, int dtype, void* xt, void* yt, void* coef, cudaStream_t s);
 // program construction helpers (program.cu)
 void stage_set(Stage& st, std::vector<OpDesc> ops, DevBuf&& mats, int64_t elems, int elem_bytes, cudaStream_t s);
 void program_totals(Program& p);
+void program_check(const Program& p);
+bool program_finite(const Program& p, cudaStream_t s);  // every stored factor entry finite  // every block inside its vector spaces and matrix buffer (host)
 void program_adjoint(const Program& fwd, Program& adj, cudaStream_t s);
 void program_filter(const Program& src, int32_t tag, Program& out, cudaStream_t s);
 void program_relocate_coef(Program& p, int64_t shift, cudaStream_t s);
+void program_compact_coef(Program& p, cudaStream_t s);  // coefficient memory shared by lifetime
+void program_restrict_rows(const Program& p, int64_t lo, int64_t hi, Program& out, cudaStream_t s);
 void program_append(Program& dst, Program&& src, cudaStream_t s);
 void program_prepend(Program& dst, Program&& src);
 // same, with the stage launches replayed from a cached CUDA graph
@@ -327,6 +334,13 @@ void build_hodbf(vie_op* h, cudaStream_t s, BuildResult& res);
 void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src, double tol, Program& P,
                    bool leaf_blocks, int v0_space, cudaStream_t s, BuildResult& res);
 void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res);
+void shard_forget(const vie_op* h);  // drop the operator's sharded sub-programs
+struct InverseProductStats {
+  int levels = 0;         // Algorithm 1 levels built from products
+  int64_t products = 0;   // columns multiplied by an operator or its adjoint
+  double seconds = 0, id_seconds = 0;
+};
+void build_inverse_products(vie_op* h, int l_top, double tol, cudaStream_t s, InverseProductStats& st);
 void ensure_ws(vie_op* h, const Program& p, int64_t nrhs, int dtype);
 void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dtype, cudaStream_t s);
 void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int restart, int max_iter,
@@ -345,6 +359,8 @@ struct vie_op {
   vie::DevBuf perm;      // int32 tree -> original
   vie::DevBuf tet_faces; // int32 4*nt
   vie::Program z, zinv;
+  vie::Program zh, zinvh;   // adjoint programs, built on the first adjoint apply
+  bool zh_ready = false, zinvh_ready = false;
   bool has_zinv = false;
   int zinv_top_level = 0;   // Algorithm 1 levels l >= this are in Zinv
   vie::DevBuf xt, yt, coef;  // apply workspaces (grown on demand)

@@ -268,10 +268,11 @@ void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
     for (size_t i = 0; i + 1 < t.bounds[l].size(); ++i) big = std::max<int64_t>(big, t.bounds[l][i + 1] - t.bounds[l][i]);
     return big;
   };
+  const int64_t limit = h->cfg.inv_dense_max > 0 ? h->cfg.inv_dense_max : kDenseInverseLimit;
   int l_min = 0;
   while (l_min < LH) {
     const int64_t big = level_max(l_min);
-    if (big <= kDenseInverseLimit && 2 * big * big * (int64_t)sizeof(float2) <= room) break;
+    if (big <= limit && 2 * big * big * (int64_t)sizeof(float2) <= room) break;
     ++l_min;
   }
   h->zinv_top_level = l_min;
@@ -359,6 +360,16 @@ void build_inverse(vie_op* h, cudaStream_t s, BuildResult& res) {
       build_program(h, specs, src, h->cfg.tol_fact, P, /*leaf_blocks=*/false, SP_Y, s, res);
       i0 = i;
     }
+  }
+  program_compact_coef(P, s);
+  // levels above: from products only (Algorithm 1 line 7, Algorithm 2), no dense E_tau
+  if (l_min > 0 && h->cfg.factor_dtype == VIE_C64) {
+    InverseProductStats ps;
+    build_inverse_products(h, l_min - 1, h->cfg.tol_fact, s, ps);
+    h->zinv_top_level = 0;
+    h->stats.zinv_product_levels = ps.levels;
+    h->stats.inverse_products = ps.products;
+    h->stats.invert_product_seconds = ps.seconds;
   }
   h->has_zinv = true;
 }

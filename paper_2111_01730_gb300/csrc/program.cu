@@ -62,6 +62,11 @@ __global__ void adjoint_pack_kernel(const AdjJob* jobs, const T* src, T* dst) {
   }
 }
 
+__global__ void nonfinite_kernel(const float* v, int64_t n, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[i])) { *flag = 1; return; }
+}
+
 template <class J>
 void upload(DevBuf& b, const std::vector<J>& v, cudaStream_t s) {
   b.alloc(sizeof(J) * std::max<size_t>(1, v.size()));
@@ -89,6 +94,40 @@ void stage_set(Stage& st, std::vector<OpDesc> ops, DevBuf&& mats, int64_t elems,
   if (st.host_tag.size() != st.host_ops.size()) st.host_tag.assign(st.host_ops.size(), -1);
   st.tc_items = st.tc_bytes = st.rest_ntiles = 0;
   VIE_CUDA(cudaStreamSynchronize(s));
+}
+
+void program_check(const Program& p) {
+  const int64_t eb = elem_bytes_of(p);
+  for (size_t k = 0; k < p.stages.size(); ++k) {
+    const Stage& st = p.stages[k];
+    const int64_t elems = (int64_t)st.mats.bytes / eb;
+    for (const OpDesc& o : st.host_ops) {
+      auto fits = [&](int sp, int64_t off, int64_t len) {
+        const int64_t lim = sp == SP_C ? p.ncoef : p.n;
+        return (sp == SP_X || sp == SP_Y || sp == SP_C) && off >= 0 && len >= 0 && off + len <= lim;
+      };
+      const bool ok = o.M >= 0 && o.K >= 0 && o.ld >= o.K && (o.ld & 1) == 0 && (o.mat_off & 1) == 0 &&
+                      o.mat_off >= 0 && o.mat_off + (int64_t)o.M * o.ld <= elems && fits(o.in_space, o.in_off, o.K) &&
+                      fits(o.out_space, o.out_off, o.M);
+      VIE_REQUIRE(ok, VIE_EINVAL, "apply program block out of range (stage " + std::to_string(k) + ")");
+    }
+  }
+}
+
+bool program_finite(const Program& p, cudaStream_t s) {
+  DevBuf flag;
+  flag.alloc(sizeof(int));
+  VIE_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+  for (const Stage& st : p.stages) {
+    const int64_t n = (int64_t)(st.mats.bytes / sizeof(float));
+    if (n) nonfinite_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(st.mats.as<float>(), n,
+                                                                                             flag.as<int>());
+  }
+  VIE_CUDA(cudaGetLastError());
+  int h = 0;
+  VIE_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VIE_CUDA(cudaStreamSynchronize(s));
+  return h == 0;
 }
 
 void program_totals(Program& p) {
@@ -169,7 +208,43 @@ void program_adjoint(const Program& fwd, Program& adj, cudaStream_t s) {
       stage_set(adj.stages.back(), std::move(aops), std::move(mats), off, eb, s);
     }
   }
+  // The first adjoint block writing a coefficient interval assigns instead of adding: the
+  // coefficients then need no zero from the caller and their memory can be shared by
+  // lifetime (the forward program may already share it).  In execution order, a write is the
+  // first of its interval when no write to that interval is pending, a pending write being
+  // one that no block has read since; the second child of a pair then adds to the first.
+  {
+    std::map<int64_t, int64_t> pending;  // written, not yet read: lo -> hi
+    for (Stage& st : adj.stages) {
+      for (const OpDesc& o : st.host_ops)  // reads of this launch consume pending writes
+        if (o.in_space == SP_C && o.K > 0) {
+          const int64_t a = o.in_off, b = o.in_off + o.K;
+          auto it = pending.upper_bound(a);
+          if (it != pending.begin() && std::prev(it)->second > a) --it;
+          while (it != pending.end() && it->first < b) it = pending.erase(it);
+        }
+      bool changed = false;
+      for (OpDesc& o : st.host_ops) {
+        if (o.out_space != SP_C || o.M <= 0) continue;
+        const int64_t a = o.out_off, b = o.out_off + o.M;
+        auto it = pending.find(a);
+        if (it != pending.end() && it->second == b) continue;  // adds to the pending write
+        auto nx = pending.upper_bound(a);
+        const bool clash = (nx != pending.end() && nx->first < b) ||
+                           (nx != pending.begin() && std::prev(nx)->second > a);
+        VIE_REQUIRE(!clash, VIE_EINVAL, "adjoint program: overlapping coefficient writes of different extent");
+        pending[a] = b;
+        o.accumulate = 0;
+        changed = true;
+      }
+      if (changed)
+        VIE_CUDA(cudaMemcpyAsync(st.ops.p, st.host_ops.data(), sizeof(OpDesc) * st.host_ops.size(),
+                                 cudaMemcpyHostToDevice, s));
+    }
+    VIE_CUDA(cudaStreamSynchronize(s));
+  }
   program_totals(adj);
+  program_check(adj);
 }
 
 void program_filter(const Program& src, int32_t tag, Program& out, cudaStream_t s) {
@@ -235,6 +310,215 @@ void program_filter(const Program& src, int32_t tag, Program& out, cudaStream_t 
   }
   out.ncoef = nc;
   program_totals(out);
+  program_check(out);
+}
+
+// Coefficient space by lifetimes.  A unit is a maximal run of coefficients that
+// some block reads or writes as part of one interval.  A unit whose first access
+// (in stage order) is a set of assigning writes covering all of it, and that some
+// block reads later, carries nothing in from before; it is live from that stage to
+// its last access and may share memory with units whose lives end earlier.  Any
+// other unit keeps memory of its own (it relies on the zero the caller sets before
+// the run).  The adjoint program of a compacted program keeps these offsets: its
+// lifetimes are the same intervals reversed, and program_adjoint makes the first
+// write of every unit an assignment.  Units with the
+// same (first, last) stages are packed together in their original order, which
+// keeps every interval a block reads across adjacent units contiguous.
+void program_compact_coef(Program& p, cudaStream_t s) {
+  struct Acc { int64_t lo, hi; int stage; bool write, assign; };
+  std::vector<Acc> acc;
+  for (size_t k = 0; k < p.stages.size(); ++k)
+    for (const OpDesc& o : p.stages[k].host_ops) {
+      if (o.in_space == SP_C && o.K > 0) acc.push_back(Acc{o.in_off, o.in_off + o.K, (int)k, false, false});
+      if (o.out_space == SP_C && o.M > 0) acc.push_back(Acc{o.out_off, o.out_off + o.M, (int)k, true, o.accumulate == 0});
+    }
+  if (acc.empty()) { p.ncoef = 0; return; }
+  std::vector<size_t> ord(acc.size());
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return acc[a].lo < acc[b].lo; });
+  struct Unit { int64_t lo, hi; int first = 1 << 30, last = -1; bool init = false, read = false; int64_t base = 0; };
+  std::vector<Unit> units;
+  std::vector<int> unit_of(acc.size());
+  for (size_t q : ord) {
+    if (units.empty() || acc[q].lo >= units.back().hi) units.push_back(Unit{acc[q].lo, acc[q].hi});
+    else units.back().hi = std::max(units.back().hi, acc[q].hi);
+    unit_of[q] = (int)units.size() - 1;
+  }
+  for (size_t q = 0; q < acc.size(); ++q) {
+    Unit& u = units[unit_of[q]];
+    u.first = std::min(u.first, acc[q].stage);
+    u.last = std::max(u.last, acc[q].stage);
+    if (!acc[q].write) u.read = true;
+  }
+  {  // self-initializing: the accesses of the first stage are assigning writes covering the unit
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> cover(units.size());
+    std::vector<char> bad(units.size(), 0);
+    for (size_t q = 0; q < acc.size(); ++q) {
+      const int ui = unit_of[q];
+      if (acc[q].stage != units[ui].first) continue;
+      if (!acc[q].write || !acc[q].assign) bad[ui] = 1;
+      else cover[ui].push_back({acc[q].lo, acc[q].hi});
+    }
+    for (size_t ui = 0; ui < units.size(); ++ui) {
+      if (bad[ui]) continue;
+      auto& cv = cover[ui];
+      std::sort(cv.begin(), cv.end());
+      int64_t reach = units[ui].lo;
+      for (auto& c : cv) {
+        if (c.first > reach) break;
+        reach = std::max(reach, c.second);
+      }
+      // a unit no block reads is read first in the adjoint program (which takes its offsets
+      // from this one) and must hold the zero the caller sets: it keeps memory of its own
+      units[ui].init = reach >= units[ui].hi && units[ui].read;
+    }
+  }
+  // exclusive memory first, then lifetime groups placed first-fit over freed regions
+  int64_t top = 0;
+  for (Unit& u : units)
+    if (!u.init) { u.base = top; top += u.hi - u.lo; }
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (size_t ui = 0; ui < units.size(); ++ui)
+    if (units[ui].init) groups[{units[ui].first, units[ui].last}].push_back((int)ui);
+  struct Region { int64_t addr, size; int last; };
+  std::vector<Region> busy;
+  std::vector<std::pair<int64_t, int64_t>> freel;  // (addr, size)
+  for (auto& g : groups) {  // ordered by first stage
+    const int first = g.first.first, last = g.first.second;
+    for (size_t i = 0; i < busy.size();) {
+      if (busy[i].last < first) { freel.push_back({busy[i].addr, busy[i].size}); busy.erase(busy.begin() + i); }
+      else ++i;
+    }
+    std::sort(freel.begin(), freel.end());
+    std::vector<std::pair<int64_t, int64_t>> merged;
+    for (auto& f : freel) {
+      if (!merged.empty() && merged.back().first + merged.back().second == f.first) merged.back().second += f.second;
+      else merged.push_back(f);
+    }
+    freel = merged;
+    int64_t need = 0;
+    for (int ui : g.second) need += units[ui].hi - units[ui].lo;
+    int64_t addr = -1;
+    for (size_t i = 0; i < freel.size(); ++i)
+      if (freel[i].second >= need) {
+        addr = freel[i].first;
+        freel[i].first += need;
+        freel[i].second -= need;
+        if (freel[i].second == 0) freel.erase(freel.begin() + i);
+        break;
+      }
+    if (addr < 0) { addr = top; top += need; }
+    int64_t off = addr;
+    for (int ui : g.second) { units[ui].base = off; off += units[ui].hi - units[ui].lo; }
+    busy.push_back(Region{addr, need, last});
+  }
+  auto remap = [&](int64_t lo) {
+    auto it = std::upper_bound(units.begin(), units.end(), lo, [](int64_t v, const Unit& u) { return v < u.lo; });
+    --it;
+    return it->base + (lo - it->lo);
+  };
+  for (Stage& st : p.stages) {
+    bool changed = false;
+    for (OpDesc& o : st.host_ops) {
+      if (o.in_space == SP_C && o.K > 0) { o.in_off = remap(o.in_off); changed = true; }
+      if (o.out_space == SP_C && o.M > 0) { o.out_off = remap(o.out_off); changed = true; }
+      if (o.in_space == SP_C && o.K == 0) o.in_off = 0;
+    }
+    if (changed && !st.host_ops.empty())
+      VIE_CUDA(cudaMemcpyAsync(st.ops.p, st.host_ops.data(), sizeof(OpDesc) * st.host_ops.size(),
+                               cudaMemcpyHostToDevice, s));
+    st.tc_tiles.release(); st.tc_ops.release(); st.rest_ops.release(); st.rest_tiles.release();
+    st.tc_items = st.tc_bytes = st.rest_ntiles = 0;
+  }
+  p.tc_ready = false;
+  for (auto& g : p.graphs)
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+  p.ncoef = top;
+  VIE_CUDA(cudaStreamSynchronize(s));
+  program_check(p);
+}
+
+// The blocks of a program that the output rows [lo, hi) of Y depend on (their dependency
+// closure, found backwards through the stages), copied with their matrices into `out`;
+// coefficient offsets are kept (out.ncoef = p.ncoef).  For Z the closure writes Y only
+// on [lo, hi); a program that reads Y (the in-place levels of Zinv) may also need, and
+// then writes, other rows of Y, which the caller discards.  The restricted program reads
+// X wherever the kept blocks read it (the caller provides the whole of X).
+void program_restrict_rows(const Program& p, int64_t lo, int64_t hi, Program& out, cudaStream_t s) {
+  const int eb = elem_bytes_of(p);
+  // needed intervals per space (C, Y): map lo -> hi, disjoint and merged
+  std::map<int64_t, int64_t> need[3];
+  auto overlaps = [&](int sp, int64_t a, int64_t b) {
+    auto& m = need[sp];
+    auto it = m.upper_bound(a);
+    if (it != m.begin()) { auto pv = std::prev(it); if (pv->second > a) return true; }
+    return it != m.end() && it->first < b;
+  };
+  auto add = [&](int sp, int64_t a, int64_t b) {
+    if (b <= a) return;
+    auto& m = need[sp];
+    auto it = m.upper_bound(a);
+    if (it != m.begin()) {
+      auto pv = std::prev(it);
+      if (pv->second >= a) { a = pv->first; b = std::max(b, pv->second); it = m.erase(pv); }
+    }
+    while (it != m.end() && it->first <= b) { b = std::max(b, it->second); it = m.erase(it); }
+    m[a] = b;
+  };
+  add(SP_Y, lo, hi);
+  std::vector<std::vector<char>> keep(p.stages.size());
+  for (int k = (int)p.stages.size() - 1; k >= 0; --k) {
+    const auto& ops = p.stages[k].host_ops;
+    keep[k].assign(ops.size(), 0);
+    std::vector<size_t> kept;
+    for (size_t i = 0; i < ops.size(); ++i) {
+      const OpDesc& o = ops[i];
+      if (o.M <= 0) continue;
+      if (o.out_space != SP_X && overlaps(o.out_space, o.out_off, o.out_off + o.M)) { keep[k][i] = 1; kept.push_back(i); }
+    }
+    for (size_t i : kept) {  // inputs of this stage's kept blocks are needed from earlier stages
+      const OpDesc& o = ops[i];
+      if (o.in_space != SP_X && o.K > 0) add(o.in_space, o.in_off, o.in_off + o.K);
+    }
+  }
+  out.stages.clear();
+  out.n = p.n;
+  out.ncoef = p.ncoef;
+  out.factor_dtype = p.factor_dtype;
+  out.tc_ready = false;
+  for (size_t k = 0; k < p.stages.size(); ++k) {
+    const Stage& st = p.stages[k];
+    std::vector<OpDesc> ops;
+    std::vector<int32_t> tags;
+    std::vector<CopyJob> jobs;
+    int64_t off = 0;
+    for (size_t i = 0; i < st.host_ops.size(); ++i) {
+      if (!keep[k][i]) continue;
+      OpDesc o = st.host_ops[i];
+      const int64_t cnt = (int64_t)o.M * o.ld;
+      jobs.push_back(CopyJob{o.mat_off, off, cnt});
+      o.mat_off = off;
+      off += cnt;
+      off = (off + 1) & ~int64_t(1);
+      ops.push_back(o);
+      tags.push_back(i < st.host_tag.size() ? st.host_tag[i] : -1);
+    }
+    if (ops.empty()) continue;
+    DevBuf mats, dj;
+    mats.alloc(std::max<int64_t>(off, 2) * eb);
+    upload(dj, jobs, s);
+    if (eb == 8)
+      copy_jobs_kernel<float2><<<(int)jobs.size(), 256, 0, s>>>(dj.as<CopyJob>(), st.mats.as<float2>(), mats.as<float2>());
+    else
+      copy_jobs_kernel<double2><<<(int)jobs.size(), 256, 0, s>>>(dj.as<CopyJob>(), st.mats.as<double2>(),
+                                                                 mats.as<double2>());
+    VIE_CUDA(cudaGetLastError());
+    out.stages.emplace_back();
+    out.stages.back().host_tag = tags;
+    stage_set(out.stages.back(), std::move(ops), std::move(mats), off, eb, s);
+  }
+  program_totals(out);
+  program_check(out);
 }
 
 void program_relocate_coef(Program& p, int64_t shift, cudaStream_t s) {

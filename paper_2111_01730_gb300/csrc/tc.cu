@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(kThreads, 4) tc_stage_kernel(const TcItem* __r
     const uint32_t tile_bytes = 4u * it.n * kKc * 2u;
     if (tid < it.mc) {  // output row pointers of the item, resolved once
       const TcSeg& sg = it.seg[seg_of(it, tid)];
-      s_dst[tid] = (sg.out_space == SP_Y ? yt : coef) + (sg.out_off + sg.row0 + tid - sg.start) * nrhs;
+      s_dst[tid] = (sg.out_space == SP_Y ? yt : (sg.out_space == SP_X ? const_cast<float2*>(xt) : coef)) +
+                   (sg.out_off + sg.row0 + tid - sg.start) * nrhs;
       s_acc[tid] = sg.accumulate;
     }
     for (int kc = 0; kc < nk && ok; ++kc) {

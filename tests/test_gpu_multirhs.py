@@ -62,3 +62,25 @@ def test_tensor_core_apply_mid_size_matches_single_rhs(op_mid, nrhs):
     ref = torch.stack([op.apply(X[:, j].contiguous()) for j in cols], 1)
     err = (torch.linalg.norm(Y[:, cols] - ref) / torch.linalg.norm(ref)).item()
     assert err < 2e-5, err
+
+
+def test_precision_selector():
+    """vie_config.prec: FP64 stores complex FP64 factors, C32 never takes the tensor cores (its
+    16-column apply equals 16 single-column applies), BF16x3 takes them from 16 columns, TF32 is
+    refused as not built."""
+    body = W.sphere(0.2, 4.0 - 1.0j, 1.0 / 16)
+    X = torch.from_numpy(W.random_block(1824, 16, seed=9)).to(torch.complex64).cuda().t().contiguous().t()
+    c32 = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, prec=pkg.VIE_P_C32)
+    assert c32.autotune_rhs() >= 1 << 30
+    Y = c32.apply(X)
+    cols = torch.stack([c32.apply(X[:, j].contiguous()) for j in range(16)], 1)
+    assert (torch.linalg.norm(Y - cols) / torch.linalg.norm(cols)).item() < 1e-6
+    tc = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, prec=pkg.VIE_P_TC_BF16X3)
+    assert tc.autotune_rhs() == 16
+    err = (torch.linalg.norm(tc.apply(X) - cols) / torch.linalg.norm(cols)).item()
+    assert 0 < err < 5e-5  # BF16x3 split products: close to, not equal to, the FP32 result
+    f64 = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, prec=pkg.VIE_P_FP64)
+    assert f64.get_stats().bytes_z > 1.8 * tc.get_stats().bytes_z  # complex FP64 factors
+    with pytest.raises(pkg.VieError) as e:
+        pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, prec=pkg.VIE_P_TC_TF32)
+    assert e.value.status == pkg.VIE_ENOTSUP

@@ -1,10 +1,7 @@
 """Full-size parity of the plasma-shell workload (outer 1.5, inner 1.2 lambda0, Drude eps_r, vacuum
-core, pitch lambda0/20, N = 690,768): the 128-right-hand-side tensor-core apply, checked on sampled
-output rows that the oracle computes one by one from Eq. 5.
-
-With every ID truncated at chi_con = 1e-4 itself the apply error of this 14-level operator is
-1.1e-3 on 8 sampled rows (5.7e-4 at chi_con / 2), above the 5e-4 bound; the operator here is built
-with each ID truncated at chi_con / 3 (vie_config.id_tol_div = 3)."""
+core, pitch lambda0/20, N = 690,768): the 128-right-hand-side tensor-core apply, checked on 64
+sampled output rows that the oracle computes from Eq. 5, with the builder settings of the benchmark
+(every ID of Z truncated at chi_con / 3, the one constant used for every workload)."""
 import numpy as np
 import pytest
 
@@ -17,14 +14,14 @@ if not torch.cuda.is_available():
     pytest.skip("no GPU", allow_module_level=True)
 
 import paper_2111_01730_gb300 as pkg  # noqa: E402
-from oracle.entries import Elements, zblock  # noqa: E402
 from oracle.mesh import build_mesh  # noqa: E402
+from oracle_pool import z_rows  # noqa: E402
 
 
 @pytest.fixture(scope="module")
 def shell():
     body = W.plasma_shell()
-    op = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c64", seed=1, id_tol_div=3)
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, leaf=64, factor_dtype="c64", seed=1)
     yield body, op, build_mesh(body)
     op.close()
 
@@ -37,11 +34,10 @@ def test_plasma_shell_tensor_core_apply_sampled_rows(shell):
     X = torch.from_numpy(Xh.astype(np.complex64)).cuda().t().contiguous().t()
     Y = op.apply(X)          # 128 right-hand sides: tensor-core stages
     op.check()
-    rows = np.random.default_rng(8).choice(n, size=6, replace=False)
-    E = Elements(mesh, W.K0)
-    Zr = np.concatenate([zblock(E, [r], np.arange(n), chunk=2) for r in rows])
-    exact = Zr @ Xh
+    rows = np.random.default_rng(8).choice(n, size=64, replace=False)
+    exact = z_rows(body, W.K0, rows) @ Xh
     got = Y.cpu().numpy()[rows]
     err = np.linalg.norm(got - exact) / np.linalg.norm(exact)
-    print("plasma shell 128-RHS sampled-row relative error", err)
+    per_row = np.linalg.norm(got - exact, axis=1) / np.linalg.norm(exact, axis=1)
+    print("plasma shell 128-RHS, 64 sampled rows: relative error", err, "worst row", per_row.max())
     assert err < 5e-4
