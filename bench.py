@@ -238,6 +238,11 @@ def serving_tol_fact(bodies):
 def run_serving(args):
     """Continuous-batching solves (C32 factors, tensor-core multi-column applies, FP64 refinement)
     against the plain FP64 one-request-at-a-time GPU solver on the same requests."""
+    print(json.dumps(serving_line(args)), flush=True)
+    return 0
+
+
+def serving_line(args):
     import torch
 
     import paper_2111_01730_gb300 as pkg
@@ -323,8 +328,7 @@ def run_serving(args):
             "plain_fp64_one_at_a_time": {"solves_per_s": round(base, 2), "sample_rhs": done_rhs,
                                          "max_relres": max(rel_b)},
             "speedup_vs_plain_fp64": round(total_rhs / wall_s / base, 2)}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def zinv_timing(op, pkg, x, y, steps, torch):

@@ -124,14 +124,15 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // Complex unit-variance Gaussian entries G[row, col0 + c] for rows in the ranges, c < ncols:
-// splitmix64 of (seed, row, column) gives two uniforms, the Box-Muller transform the pair.
-__global__ void gauss_rows_kernel(float2* g, int ld, int col0, int ncols, const RangeDev* r, int n, int64_t total,
-                                  uint64_t seed) {
+// splitmix64 of (seed, row, hcol0 + c) gives two uniforms, the Box-Muller transform the pair
+// (the sample's own column index hcol0 + c, so that a block drawn in pieces is the same block).
+__global__ void gauss_rows_kernel(float2* g, int ld, int col0, int hcol0, int ncols, const RangeDev* r, int n,
+                                  int64_t total, uint64_t seed) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total * ncols;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = range_row(r, n, e / ncols);
     const int c = int(e % ncols);
-    const uint64_t hsh = mix64(seed ^ mix64((uint64_t)row * 0x100000001B3ull + (uint64_t)(col0 + c)));
+    const uint64_t hsh = mix64(seed ^ mix64((uint64_t)row * 0x100000001B3ull + (uint64_t)(hcol0 + c)));
     const float u1 = ((uint32_t)(hsh >> 40) + 1u) * (1.0f / 16777217.0f);
     const float u2 = (uint32_t)(hsh & 0xFFFFFFu) * (1.0f / 16777216.0f);
     const float rad = sqrtf(-logf(u1));
@@ -148,33 +149,56 @@ __global__ void unit_rows_kernel(float2* g, int ld, int q0, int ncols, const Ran
     if (rg.lo + q0 + c < rg.hi) g[(rg.lo + q0 + c) * ld + c] = make_float2(1.f, 0.f);
 }
 
-// sketch gather into an FP64 ID pool: out[off + q + c m] = (conj) V[idx[c] * ld + q0 + q]
+// sketch gather into an FP64 ID pool, one piece of sample rows at a time:
+// out[off + row0 + q + c m] = (conj) V[idx[c] * ld + q0 + q] for q < mq, c < n (m x n column-major)
 struct GatherJob {
   int64_t out_off, idx_off;
-  int32_t n, m, q0, conj;
+  int32_t n, m, q0, conj, row0, mq;
 };
 
 __global__ void sketch_gather_kernel(const GatherJob* jobs, const int32_t* idx, const float2* V, int ld, double2* out) {
   const GatherJob j = jobs[blockIdx.x];
-  for (int64_t e = threadIdx.x; e < (int64_t)j.m * j.n; e += blockDim.x) {
-    const int q = int(e % j.m), c = int(e / j.m);
+  for (int64_t e = threadIdx.x; e < (int64_t)j.mq * j.n; e += blockDim.x) {
+    const int q = int(e % j.mq), c = int(e / j.mq);
     const float2 v = V[(int64_t)idx[j.idx_off + c] * ld + j.q0 + q];
-    out[j.out_off + e] = make_double2(v.x, j.conj ? -v.y : v.y);
+    out[j.out_off + j.row0 + q + (int64_t)c * j.m] = make_double2(v.x, j.conj ? -v.y : v.y);
   }
 }
 
-// coefficient gather for the middle level: out[off + q + c m] = conj(C[(coff + c) * ld + q0 + q])
+// coefficient gather for the middle level: out[off + row0 + q + c m] = conj(C[(coff + c) * ld + q0 + q])
 struct CoefJob {
   int64_t out_off, coff;
-  int32_t rows, m, q0, pad;
+  int32_t rows, m, q0, row0, mq, pad;
 };
 
 __global__ void coef_gather_kernel(const CoefJob* jobs, const float2* C, int ld, double2* out) {
   const CoefJob j = jobs[blockIdx.x];
-  for (int64_t e = threadIdx.x; e < (int64_t)j.m * j.rows; e += blockDim.x) {
-    const int q = int(e % j.m), c = int(e / j.m);
+  for (int64_t e = threadIdx.x; e < (int64_t)j.mq * j.rows; e += blockDim.x) {
+    const int q = int(e % j.mq), c = int(e / j.mq);
     const float2 v = C[(j.coff + c) * ld + j.q0 + q];
-    out[j.out_off + e] = make_double2(v.x, -v.y);
+    out[j.out_off + j.row0 + q + (int64_t)c * j.m] = make_double2(v.x, -v.y);
+  }
+}
+
+// [A | B] of one least-squares job: A (m x nc) copied from the column-chain pool, B (m x nr)
+// = conj of the sample rows of the chosen skeleton rows, read from a copy of the ID pool
+struct AssembleJob {
+  int64_t ab_off, cg_off, x_off, piv_off;
+  int32_t m, nc, nr, pad;
+};
+
+__global__ void lsq_assemble_kernel(const AssembleJob* jobs, const double2* cg, const double2* xs,
+                                    const int32_t* piv, double2* ab) {
+  const AssembleJob j = jobs[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < (int64_t)j.m * (j.nc + j.nr); e += blockDim.x) {
+    const int q = int(e % j.m), c = int(e / j.m);
+    double2 v;
+    if (c < j.nc) v = cg[j.cg_off + e];
+    else {
+      v = xs[j.x_off + q + (int64_t)piv[j.piv_off + c - j.nc] * j.m];
+      v.y = -v.y;
+    }
+    ab[j.ab_off + e] = v;
   }
 }
 
@@ -564,31 +588,14 @@ std::unique_ptr<ProgOp> rbf_build(Ctx& c, LinOp& A, int lam, const std::vector<i
     const int k = std::max(kl + p, 16);
     colV[l].resize(cand.size());
     std::vector<std::vector<int32_t>> nskel(cand.size());
-    // chunks of whole row blocks i
+    // batches of whole row blocks i (one block when its samples alone exceed a product); the
+    // k samples of a block are drawn in pieces of at most kProdCols columns
     const int per = std::max(1, kProdCols / k);
+    const int qstep = std::min(k, kProdCols);
     for (int64_t i0 = 0; i0 < ni; i0 += per) {
       const int64_t i1 = std::min<int64_t>(ni, i0 + per);
-      const int kc = (int)(i1 - i0) * k;
-      Vec G(c, kc), S(c, kc);
-      rows_op(c, V_ZERO, G.p, nullptr, kc, orows);
-      for (int64_t i = i0; i < i1; ++i) {
-        std::vector<std::pair<int64_t, int64_t>> rv;
-        for (int b = 0; b < B; ++b) {
-          const int64_t g = onodes[b] * ni + i;
-          rv.push_back({c.node_lo(lam + l, g), c.node_hi(lam + l, g)});
-        }
-        Ranges rr;
-        rr.set(rv, c.s);
-        if (rr.rows)
-          gauss_rows_kernel<<<gridn(rr.rows * k), 256, 0, c.s>>>(G.p, kc, (int)(i - i0) * k, k, rr.d.as<RangeDev>(),
-                                                                 (int)rr.r.size(), rr.rows,
-                                                                 seed ^ (0xA5A5ull << 32) ^ ((uint64_t)l << 48) ^ (uint64_t)i);
-        VIE_CUDA(cudaGetLastError());
-        VIE_CUDA(cudaStreamSynchronize(c.s));  // rr is released at the end of this iteration
-      }
-      A.rmv(G.p, S.p, kc);
-      // sketch gather: job (b, i, j) -> m = k rows (samples), n = |cand| columns
       std::vector<GatherJob> gj;
+      std::vector<int64_t> gi;  // block i of each job
       std::vector<int32_t> idx;
       std::vector<std::pair<int64_t, std::pair<int, int>>> jobs;
       std::vector<size_t> jq;
@@ -599,7 +606,8 @@ std::unique_ptr<ProgOp> rbf_build(Ctx& c, LinOp& A, int lam, const std::vector<i
             const size_t q = ((size_t)b * ni + i) * nj + j;
             const auto& cd = cand[q];
             if (cd.empty()) continue;
-            gj.push_back(GatherJob{aoff, (int64_t)idx.size(), (int32_t)cd.size(), k, (int32_t)((i - i0) * k), 1});
+            gj.push_back(GatherJob{aoff, (int64_t)idx.size(), (int32_t)cd.size(), k, 0, 1, 0, 0});
+            gi.push_back(i);
             idx.insert(idx.end(), cd.begin(), cd.end());
             jobs.push_back({aoff, {k, (int)cd.size()}});
             jq.push_back(q);
@@ -608,11 +616,40 @@ std::unique_ptr<ProgOp> rbf_build(Ctx& c, LinOp& A, int lam, const std::vector<i
       if (jobs.empty()) continue;
       DevBuf A64, dgj, didx;
       A64.alloc(sizeof(double2) * aoff);
-      upload_vec(dgj, gj, c.s);
       upload_vec(didx, idx, c.s);
-      sketch_gather_kernel<<<(int)gj.size(), 256, 0, c.s>>>(dgj.as<GatherJob>(), didx.as<int32_t>(), S.p, kc,
-                                                            A64.as<double2>());
-      VIE_CUDA(cudaGetLastError());
+      for (int q0 = 0; q0 < k; q0 += qstep) {
+        const int kq = std::min(qstep, k - q0);
+        const int kc = (int)(i1 - i0) * kq;
+        Vec G(c, kc), S(c, kc);
+        rows_op(c, V_ZERO, G.p, nullptr, kc, orows);
+        for (int64_t i = i0; i < i1; ++i) {
+          std::vector<std::pair<int64_t, int64_t>> rv;
+          for (int b = 0; b < B; ++b) {
+            const int64_t g = onodes[b] * ni + i;
+            rv.push_back({c.node_lo(lam + l, g), c.node_hi(lam + l, g)});
+          }
+          Ranges rr;
+          rr.set(rv, c.s);
+          if (rr.rows)
+            gauss_rows_kernel<<<gridn(rr.rows * kq), 256, 0, c.s>>>(
+                G.p, kc, (int)(i - i0) * kq, q0, kq, rr.d.as<RangeDev>(), (int)rr.r.size(), rr.rows,
+                seed ^ (0xA5A5ull << 32) ^ ((uint64_t)l << 48) ^ (uint64_t)i);
+          VIE_CUDA(cudaGetLastError());
+          VIE_CUDA(cudaStreamSynchronize(c.s));  // rr is released at the end of this iteration
+        }
+        A.rmv(G.p, S.p, kc);
+        // job (b, i, j): rows q0 .. q0 + kq of its k x |cand| row sketch
+        for (size_t u = 0; u < gj.size(); ++u) {
+          gj[u].q0 = (int32_t)((gi[u] - i0) * kq);
+          gj[u].row0 = q0;
+          gj[u].mq = kq;
+        }
+        upload_vec(dgj, gj, c.s);
+        sketch_gather_kernel<<<(int)gj.size(), 256, 0, c.s>>>(dgj.as<GatherJob>(), didx.as<int32_t>(), S.p, kc,
+                                                              A64.as<double2>());
+        VIE_CUDA(cudaGetLastError());
+        VIE_CUDA(cudaStreamSynchronize(c.s));
+      }
       std::vector<VRef> refs;
       std::vector<std::vector<int32_t>> piv;
       run_ids(A64, jobs, refs, piv);
@@ -738,28 +775,12 @@ std::unique_ptr<ProgOp> rbf_build(Ctx& c, LinOp& A, int lam, const std::vector<i
     std::vector<std::vector<int32_t>> nsk(cand.size());
     if (last) midV.resize((size_t)B * (int64_t(1) << h) * nj);
     const int per = std::max(1, kProdCols / k);
+    const int qstep = std::min(k, kProdCols);
+    const int64_t nih = int64_t(1) << h;
     for (int64_t j0 = 0; j0 < nj; j0 += per) {
       const int64_t j1 = std::min<int64_t>(nj, j0 + per);
-      const int kc = (int)(j1 - j0) * k;
-      Vec G(c, kc), X(c, kc);
-      rows_op(c, V_ZERO, G.p, nullptr, kc, scols);
-      for (int64_t j = j0; j < j1; ++j) {
-        std::vector<std::pair<int64_t, int64_t>> rv;
-        for (int b = 0; b < B; ++b) {
-          const int64_t g = snodes[b] * nj + j;
-          rv.push_back({c.node_lo(lam + t, g), c.node_hi(lam + t, g)});
-        }
-        Ranges rr;
-        rr.set(rv, c.s);
-        if (rr.rows)
-          gauss_rows_kernel<<<gridn(rr.rows * k), 256, 0, c.s>>>(G.p, kc, (int)(j - j0) * k, k, rr.d.as<RangeDev>(),
-                                                                 (int)rr.r.size(), rr.rows,
-                                                                 seed ^ (0x5A5Aull << 32) ^ ((uint64_t)t << 48) ^ (uint64_t)j);
-        VIE_CUDA(cudaGetLastError());
-        VIE_CUDA(cudaStreamSynchronize(c.s));
-      }
-      A.mv(G.p, X.p, kc);
       std::vector<GatherJob> gj;
+      std::vector<int64_t> gjj;  // column block j of each job
       std::vector<int32_t> idx;
       std::vector<std::pair<int64_t, std::pair<int, int>>> jobs;
       std::vector<size_t> jq;
@@ -770,73 +791,132 @@ std::unique_ptr<ProgOp> rbf_build(Ctx& c, LinOp& A, int lam, const std::vector<i
             const size_t q = ((size_t)b * ni + i) * nj + j;
             const auto& cd = cand[q];
             if (cd.empty()) continue;
-            gj.push_back(GatherJob{aoff, (int64_t)idx.size(), (int32_t)cd.size(), k, (int32_t)((j - j0) * k), 0});
+            gj.push_back(GatherJob{aoff, (int64_t)idx.size(), (int32_t)cd.size(), k, 0, 0, 0, 0});
+            gjj.push_back(j);
             idx.insert(idx.end(), cd.begin(), cd.end());
             jobs.push_back({aoff, {k, (int)cd.size()}});
             jq.push_back(q);
             aoff += (int64_t)k * cd.size();
           }
+      // middle (last step): the column chain of the same random blocks, C G_j, per pair (b, i, j)
+      std::vector<CoefJob> cj;
+      std::vector<int64_t> cjj, cgoff;
+      std::vector<size_t> cq;
+      int64_t cgn = 0;
+      if (last)
+        for (int b = 0; b < B; ++b)
+          for (int64_t i = 0; i < nih; ++i)
+            for (int64_t j = j0; j < j1; ++j) {
+              const size_t qc = ((size_t)b * nih + i) * nj + j;
+              const int rc = colV[h][qc].r;
+              if (rc == 0) continue;
+              cj.push_back(CoefJob{cgn, coff[h][qc], rc, k, 0, 0, 0, 0});
+              cjj.push_back(j);
+              cq.push_back(qc);
+              cgoff.push_back(cgn);
+              cgn += (int64_t)k * rc;
+            }
+      if (jobs.empty() && cj.empty()) continue;
+      DevBuf A64, dgj, didx, CG, dcj;
+      A64.alloc(sizeof(double2) * std::max<int64_t>(1, aoff));
+      if (cgn) CG.alloc(sizeof(double2) * cgn);
+      upload_vec(didx, idx, c.s);
+      for (int q0 = 0; q0 < k; q0 += qstep) {
+        const int kq = std::min(qstep, k - q0);
+        const int kc = (int)(j1 - j0) * kq;
+        Vec G(c, kc), X(c, kc);
+        rows_op(c, V_ZERO, G.p, nullptr, kc, scols);
+        for (int64_t j = j0; j < j1; ++j) {
+          std::vector<std::pair<int64_t, int64_t>> rv;
+          for (int b = 0; b < B; ++b) {
+            const int64_t g = snodes[b] * nj + j;
+            rv.push_back({c.node_lo(lam + t, g), c.node_hi(lam + t, g)});
+          }
+          Ranges rr;
+          rr.set(rv, c.s);
+          if (rr.rows)
+            gauss_rows_kernel<<<gridn(rr.rows * kq), 256, 0, c.s>>>(
+                G.p, kc, (int)(j - j0) * kq, q0, kq, rr.d.as<RangeDev>(), (int)rr.r.size(), rr.rows,
+                seed ^ (0x5A5Aull << 32) ^ ((uint64_t)t << 48) ^ (uint64_t)j);
+          VIE_CUDA(cudaGetLastError());
+          VIE_CUDA(cudaStreamSynchronize(c.s));
+        }
+        A.mv(G.p, X.p, kc);
+        if (!gj.empty()) {
+          for (size_t u = 0; u < gj.size(); ++u) {
+            gj[u].q0 = (int32_t)((gjj[u] - j0) * kq);
+            gj[u].row0 = q0;
+            gj[u].mq = kq;
+          }
+          upload_vec(dgj, gj, c.s);
+          sketch_gather_kernel<<<(int)gj.size(), 256, 0, c.s>>>(dgj.as<GatherJob>(), didx.as<int32_t>(), X.p, kc,
+                                                                A64.as<double2>());
+          VIE_CUDA(cudaGetLastError());
+        }
+        if (!cj.empty()) {  // the column chain only writes C
+          Vec dummyY(c, kc);
+          if (kc >= P.tc_min_rhs) program_prepare_tc(P, c.s);
+          float2* cf = c.coef_ws(P.ncoef, kc);
+          program_run(P, kc, VIE_C64, G.p, dummyY.p, cf, c.s);
+          for (size_t u = 0; u < cj.size(); ++u) {
+            cj[u].q0 = (int32_t)((cjj[u] - j0) * kq);
+            cj[u].row0 = q0;
+            cj[u].mq = kq;
+          }
+          upload_vec(dcj, cj, c.s);
+          coef_gather_kernel<<<(int)cj.size(), 256, 0, c.s>>>(dcj.as<CoefJob>(), cf, kc, CG.as<double2>());
+          VIE_CUDA(cudaGetLastError());
+        }
+        VIE_CUDA(cudaStreamSynchronize(c.s));
+      }
+      // the row IDs destroy their pool: keep a copy of the samples for the middle
+      DevBuf Xs;
+      if (last && !jobs.empty()) {
+        Xs.alloc(sizeof(double2) * aoff);
+        VIE_CUDA(cudaMemcpyAsync(Xs.p, A64.p, sizeof(double2) * aoff, cudaMemcpyDeviceToDevice, c.s));
+      }
+      std::vector<VRef> refs;
+      std::vector<std::vector<int32_t>> piv;
+      std::vector<int64_t> job_of(cand.size(), -1);
       if (!jobs.empty()) {
-        DevBuf A64, dgj, didx;
-        A64.alloc(sizeof(double2) * aoff);
-        upload_vec(dgj, gj, c.s);
-        upload_vec(didx, idx, c.s);
-        sketch_gather_kernel<<<(int)gj.size(), 256, 0, c.s>>>(dgj.as<GatherJob>(), didx.as<int32_t>(), X.p, kc,
-                                                              A64.as<double2>());
-        VIE_CUDA(cudaGetLastError());
-        std::vector<VRef> refs;
-        std::vector<std::vector<int32_t>> piv;
         run_ids(A64, jobs, refs, piv);
         for (size_t u = 0; u < jq.size(); ++u) {
           rowV[t][jq[u]] = refs[u];
+          job_of[jq[u]] = (int64_t)u;
           auto& sk = nsk[jq[u]];
           for (int32_t pv : piv[u]) sk.push_back(cand[jq[u]][pv]);
         }
       }
-      if (!last) continue;
-      // ---- middle for the pairs (b, i < 2^h, j in this chunk): M (C G_j) = X_j(I, :)
-      Vec dummyY(c, kc);
-      float2* cf = c.coef_ws(P.ncoef, kc);
-      if (kc >= P.tc_min_rhs) program_prepare_tc(P, c.s);
-      program_run(P, kc, VIE_C64, G.p, dummyY.p, cf, c.s);  // column chain only: writes C
-      std::vector<CoefJob> cj;
-      std::vector<GatherJob> xj;
-      std::vector<int32_t> xidx;
+      if (!last || cj.empty() || jobs.empty()) continue;
+      // ---- middle for the pairs (b, i < 2^h, j in this batch): M (C G_j) = X_j(I, :)
+      std::vector<AssembleJob> aj;
+      std::vector<int32_t> pvs;
       std::vector<LsqJob> lj;
       std::vector<size_t> lq;
       int64_t off2 = 0, moff2 = 0;
-      const int64_t nih = int64_t(1) << h;
-      for (int b = 0; b < B; ++b)
-        for (int64_t i = 0; i < nih; ++i)
-          for (int64_t j = j0; j < j1; ++j) {
-            const size_t qc = ((size_t)b * nih + i) * nj + j;  // column side pair at level h
-            const size_t qr = qc;                              // row side pair (row level h = L - t)
-            const int rc = colV[h][qc].r;
-            const int rr = (int)nsk[qr].size();
-            if (rc == 0 || rr == 0) continue;
-            const int q0 = (int)((j - j0) * k);
-            cj.push_back(CoefJob{off2, coff[h][qc], rc, k, q0, 0});
-            xj.push_back(GatherJob{off2 + (int64_t)k * rc, (int64_t)xidx.size(), rr, k, q0, 1});
-            xidx.insert(xidx.end(), nsk[qr].begin(), nsk[qr].end());
-            lj.push_back(LsqJob{off2, moff2, k, rc, rr, 0});
-            lq.push_back(qc);
-            off2 += (int64_t)k * (rc + rr);
-            moff2 += (int64_t)rr * rc;
-          }
+      for (size_t u = 0; u < cq.size(); ++u) {
+        const size_t qc = cq[u];  // row-side job of the same pair (row level h = L - t)
+        const int64_t jb = job_of[qc];
+        if (jb < 0 || piv[jb].empty()) continue;
+        const int rc = colV[h][qc].r, rr = (int)piv[jb].size();
+        aj.push_back(AssembleJob{off2, cgoff[u], jobs[jb].first, (int64_t)pvs.size(), k, rc, rr, 0});
+        pvs.insert(pvs.end(), piv[jb].begin(), piv[jb].end());
+        lj.push_back(LsqJob{off2, moff2, k, rc, rr, 0});
+        lq.push_back(qc);
+        off2 += (int64_t)k * (rc + rr);
+        moff2 += (int64_t)rr * rc;
+      }
       if (lj.empty()) continue;
-      DevBuf AB, dcj, dxj, dxi, dlj;
+      DevBuf AB, daj, dpv, dlj;
       pools.emplace_back(new DevBuf());
       DevBuf& Mp = *pools.back();
       AB.alloc(sizeof(double2) * off2);
       Mp.alloc(sizeof(double2) * std::max<int64_t>(1, moff2));
-      upload_vec(dcj, cj, c.s);
-      upload_vec(dxj, xj, c.s);
-      upload_vec(dxi, xidx, c.s);
+      upload_vec(daj, aj, c.s);
+      upload_vec(dpv, pvs, c.s);
       upload_vec(dlj, lj, c.s);
-      coef_gather_kernel<<<(int)cj.size(), 256, 0, c.s>>>(dcj.as<CoefJob>(), cf, kc, AB.as<double2>());
-      VIE_CUDA(cudaGetLastError());
-      sketch_gather_kernel<<<(int)xj.size(), 256, 0, c.s>>>(dxj.as<GatherJob>(), dxi.as<int32_t>(), X.p, kc,
-                                                            AB.as<double2>());
+      lsq_assemble_kernel<<<(int)aj.size(), 256, 0, c.s>>>(daj.as<AssembleJob>(), CG.as<double2>(), Xs.as<double2>(),
+                                                           dpv.as<int32_t>(), AB.as<double2>());
       VIE_CUDA(cudaGetLastError());
       lsq_kernel<256><<<(int)lj.size(), 256, 0, c.s>>>(dlj.as<LsqJob>(), AB.as<double2>(), Mp.as<double2>());
       VIE_CUDA(cudaGetLastError());

@@ -196,6 +196,17 @@ struct Server {
   cudaStream_t s = nullptr;
   DevBuf cols, packs, nrm, scale, blk_a, blk_b, hall;
   int64_t steps = 0;
+  // one stream, event pair and packed blocks per operator: the applies of different
+  // operators in one step run concurrently (fork from s, join back into s)
+  std::vector<cudaStream_t> op_s;
+  std::vector<cudaEvent_t> op_done;
+  cudaEvent_t fork = nullptr;
+  std::vector<DevBuf> op_a, op_b;
+  ~Server() {
+    for (auto st : op_s) if (st) cudaStreamDestroy(st);
+    for (auto ev : op_done) if (ev) cudaEventDestroy(ev);
+    if (fork) cudaEventDestroy(fork);
+  }
 };
 
 static size_t req_bytes(int64_t n, int nrhs, int m) {
@@ -332,8 +343,27 @@ static void arnoldi_step(Server& S) {
   if (reqs.empty()) return;
   std::map<int, std::vector<Req*>> by_op;
   for (Req* q : reqs) by_op[q->op].push_back(q);
+  if (S.op_s.empty()) {
+    S.op_s.assign(S.ops.size(), nullptr);
+    S.op_done.assign(S.ops.size(), nullptr);
+    S.op_a.resize(S.ops.size());
+    S.op_b.resize(S.ops.size());
+    for (size_t i = 0; i < S.ops.size(); ++i) {
+      VIE_CUDA(cudaStreamCreateWithFlags(&S.op_s[i], cudaStreamNonBlocking));
+      VIE_CUDA(cudaEventCreateWithFlags(&S.op_done[i], cudaEventDisableTiming));
+    }
+    VIE_CUDA(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming));
+  }
+  // fork: every operator's pack, Zinv and Z applies and unpack on its own stream, so the
+  // operators of the mix overlap on the device; join back into s before the orthogonalization
+  VIE_CUDA(cudaEventRecord(S.fork, S.s));
+  std::vector<DevBuf> descs;  // pack descriptors of every operator, alive until the step synchronizes
+  descs.reserve(2 * by_op.size());
   for (auto& kv : by_op) {
-    vie_op* h = S.ops[kv.first];
+    const int oi = kv.first;
+    vie_op* h = S.ops[oi];
+    cudaStream_t os = S.op_s[oi];
+    VIE_CUDA(cudaStreamWaitEvent(os, S.fork, 0));
     const int64_t n = h->mesh.nf;
     std::vector<PackDesc> pin, pout;
     int64_t ncol = 0;
@@ -344,26 +374,31 @@ static void arnoldi_step(Server& S) {
         ++ncol;
       }
     const size_t need = sizeof(float2) * (size_t)n * ncol;
-    if (S.blk_a.bytes < need) { S.blk_a.alloc(need); S.blk_b.alloc(need); }
-    DevBuf dpi, dpo;
+    if (S.op_a[oi].bytes < need) { S.op_a[oi].alloc(need); S.op_b[oi].alloc(need); }
+    descs.emplace_back();
+    DevBuf& dpi = descs.back();
+    descs.emplace_back();
+    DevBuf& dpo = descs.back();
     dpi.alloc(sizeof(PackDesc) * pin.size());
     dpo.alloc(sizeof(PackDesc) * pout.size());
-    VIE_CUDA(cudaMemcpyAsync(dpi.p, pin.data(), sizeof(PackDesc) * pin.size(), cudaMemcpyHostToDevice, S.s));
-    VIE_CUDA(cudaMemcpyAsync(dpo.p, pout.data(), sizeof(PackDesc) * pout.size(), cudaMemcpyHostToDevice, S.s));
+    VIE_CUDA(cudaMemcpyAsync(dpi.p, pin.data(), sizeof(PackDesc) * pin.size(), cudaMemcpyHostToDevice, os));
+    VIE_CUDA(cudaMemcpyAsync(dpo.p, pout.data(), sizeof(PackDesc) * pout.size(), cudaMemcpyHostToDevice, os));
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (n + 255) / 256)), (unsigned)ncol);
-    k_pack<<<grid, 256, 0, S.s>>>(dpi.as<PackDesc>(), (int)ncol, S.blk_a.as<float2>(), n);
-    float2 *u = S.blk_a.as<float2>(), *v = S.blk_b.as<float2>();
+    k_pack<<<grid, 256, 0, os>>>(dpi.as<PackDesc>(), (int)ncol, S.op_a[oi].as<float2>(), n);
+    float2 *u = S.op_a[oi].as<float2>(), *v = S.op_b[oi].as<float2>();
     if (h->has_zinv) {
-      op_apply(h, VIE_OP_ZINV, u, v, ncol, VIE_C64, S.s);
-      op_apply(h, VIE_OP_Z, v, u, ncol, VIE_C64, S.s);
+      op_apply(h, VIE_OP_ZINV, u, v, ncol, VIE_C64, os);
+      op_apply(h, VIE_OP_Z, v, u, ncol, VIE_C64, os);
     } else {
-      op_apply(h, VIE_OP_Z, u, v, ncol, VIE_C64, S.s);
+      op_apply(h, VIE_OP_Z, u, v, ncol, VIE_C64, os);
       std::swap(u, v);
     }
-    k_unpack<<<grid, 256, 0, S.s>>>(dpo.as<PackDesc>(), (int)ncol, u, n);
+    k_unpack<<<grid, 256, 0, os>>>(dpo.as<PackDesc>(), (int)ncol, u, n);
     VIE_CUDA(cudaGetLastError());
-    VIE_CUDA(cudaStreamSynchronize(S.s));  // the pack descriptors die with this scope
+    VIE_CUDA(cudaEventRecord(S.op_done[oi], os));
+    VIE_CUDA(cudaStreamWaitEvent(S.s, S.op_done[oi], 0));
   }
+
   // batched CGS2 over every column of every iterating request
   std::vector<ColDesc> cds;
   std::vector<std::pair<Req*, int>> who;

@@ -19,7 +19,8 @@ from oracle.entries import rhs_planewave  # noqa: E402
 def ops(lossy_sphere):
     a = pkg.Operator(lossy_sphere["body"], W.K0, tol_con=1e-5, tol_fact=1e-1, leaf=64)
     b = pkg.Operator(W.shell(0.22, 0.12, W.drude_eps(), 1.0 / 20), W.K0, tol_con=1e-5, tol_fact=1e-2, leaf=64)
-    return a, b
+    c = pkg.Operator(W.sphere(0.2, 10.0, 1.0 / 30), W.K0, tol_con=1e-5, tol_fact=1e-2, leaf=64)  # high contrast
+    return a, b, c
 
 
 def _run(srv, ids, n_of, nrhs_of, max_steps=2000):
@@ -38,37 +39,46 @@ def _run(srv, ids, n_of, nrhs_of, max_steps=2000):
 
 
 def test_same_result_alone_and_in_the_mix(ops, lossy_sphere):
-    a, b = ops
+    """Requests on three operators (a lossy sphere, a Drude shell, an eps_r = 10 sphere) whose
+    applies overlap on the device within each step; the request on the first operator gives
+    the same solution alone and in the mix, and both solutions are within 1e-3 of the oracle's
+    dense LU (residual rtol 2e-4 buys the 1e-3 solution accuracy at which the serving speed-up
+    is stated)."""
+    a, b, c = ops
+    rtol = 2e-4
     ka, pa = W.planewave_random(3, seed=31)
     Va = a.rhs_planewave(ka, pa).cpu().numpy()
-    srv = pkg.Server([a, b], restart=30, max_iter=300, mem_budget=8 << 30)
-    rid = srv.submit(0, Va, rtol=1e-3)
+    srv = pkg.Server([a, b, c], restart=30, max_iter=300, mem_budget=8 << 30)
+    rid = srv.submit(0, Va, rtol=rtol)
     alone = _run(srv, [rid], {rid: a.n}, {rid: 3})[rid]
-    assert np.all(alone[2] <= 1e-3)
-    # the same request in a mix of concurrent requests on two operators (20 columns: tensor-core applies)
+    assert np.all(alone[2] <= rtol)
+    # the same request in a mix of concurrent requests on three operators (20 columns: tensor cores)
     kb, pb = W.planewave_random(5, seed=32)
     Vb = b.rhs_planewave(kb, pb).cpu().numpy()
     kc, pc = W.planewave_random(20, seed=33)
     Vc = a.rhs_planewave(kc, pc).cpu().numpy()
-    r1 = srv.submit(1, Vb, rtol=1e-3)
-    r0 = srv.submit(0, Va, rtol=1e-3)
-    srv.step()                      # r1, r0 on the GPU ...
-    r2 = srv.submit(0, Vc, rtol=1e-3)  # ... when r2 arrives; it joins the next step
-    res = _run(srv, [r0, r1, r2], {r0: a.n, r1: b.n, r2: a.n}, {r0: 3, r1: 5, r2: 20})
+    kd, pd = W.planewave_random(4, seed=34)
+    Vd = c.rhs_planewave(kd, pd).cpu().numpy()
+    r1 = srv.submit(1, Vb, rtol=rtol)
+    r0 = srv.submit(0, Va, rtol=rtol)
+    r3 = srv.submit(2, Vd, rtol=rtol)
+    srv.step()                      # r1, r0, r3 on the GPU ...
+    r2 = srv.submit(0, Vc, rtol=rtol)  # ... when r2 arrives; it joins the next step
+    res = _run(srv, [r0, r1, r2, r3], {r0: a.n, r1: b.n, r2: a.n, r3: c.n}, {r0: 3, r1: 5, r2: 20, r3: 4})
     for r in res.values():
-        assert np.all(r[2] <= 1e-3) and r[3] > 0
+        assert np.all(r[2] <= rtol) and r[3] > 0
     mix = res[r0]
     diff = np.linalg.norm(mix[0] - alone[0]) / np.linalg.norm(alone[0])
-    assert diff <= 2e-3, diff
+    assert diff <= 1e-3, diff
     # and both against the dense LU solution of the oracle
     Io = solve_dense(lossy_sphere["Z"], rhs_planewave(lossy_sphere["E"], ka, pa))
     for r in (alone, mix):
-        assert np.linalg.norm(r[0] - Io) / np.linalg.norm(Io) <= 5e-3
+        assert np.linalg.norm(r[0] - Io) / np.linalg.norm(Io) <= 1e-3
     srv.close()
 
 
 def test_admission_by_krylov_memory(ops):
-    a, _ = ops
+    a = ops[0]
     k, p = W.planewave_random(2, seed=41)
     V = a.rhs_planewave(k, p).cpu().numpy()
     need = a.n * 2 * 16 * (10 + 6) + 4096
