@@ -88,7 +88,7 @@ typedef struct {
                             formed densely; the levels above are built from products
                             only (Algorithms 1-2 with BF_random_matvec).  0: 65,536.
                             Complex FP64 factors keep the dense construction only.  */
-  int32_t prec;          /* vie_prec (0 = VIE_P_AUTO)                                  */
+  int32_t prec;          /* a vie_prec value; 0 = VIE_P_AUTO                           */
 } vie_config;
 
 typedef struct {

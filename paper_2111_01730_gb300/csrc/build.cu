@@ -395,8 +395,9 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
         drank.alloc(sizeof(int32_t) * ij.size());
         VIE_CUDA(cudaMemcpyAsync(dij.p, ij.data(), sizeof(IdJob) * ij.size(), cudaMemcpyHostToDevice, s));
         const auto ti0 = std::chrono::steady_clock::now();
+        // the inverse's IDs (v0_space = Y, truncation at chi_fact >= 1e-3) in FP32 arithmetic
         id_batched(dij.as<IdJob>(), (int)ij.size(), maxn, dA.as<double2>(), dV.as<double2>(), dpiv.as<int32_t>(),
-                   drank.as<int32_t>(), tol_id, s);
+                   drank.as<int32_t>(), tol_id, s, /*single=*/v0_space == SP_Y && tol >= 1e-3);
         VIE_CUDA(cudaStreamSynchronize(s));
         res.t_id += std::chrono::duration<double>(std::chrono::steady_clock::now() - ti0).count();
         VIE_CUDA(cudaMemcpyAsync(piv.data(), dpiv.p, sizeof(int32_t) * poff, cudaMemcpyDeviceToHost, s));

@@ -159,7 +159,7 @@ struct IdJob {
   double tol;      // truncation |R_kk| <= tol |R_11| of this job (<= 0: the batch's tolerance)
 };
 void id_batched(const IdJob* d_jobs, int njobs, int max_n, double2* d_a, double2* d_v, int32_t* d_piv,
-                int32_t* d_rank, double tol, cudaStream_t s);
+                int32_t* d_rank, double tol, cudaStream_t s, bool single = false);
 
 // ---------------------------------------------------------------------------
 // apply program (apply.cu)

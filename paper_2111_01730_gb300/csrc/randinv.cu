@@ -31,7 +31,8 @@
 // fastest); a random block for "row node i" has entries on row node i of every
 // node of the level, and the operator's block structure keeps them apart.  All
 // products are multi-column applies of programs (tensor cores from 16 columns);
-// the IDs and the least squares run in FP64 (id_batched, lsq_kernel).
+// the least squares run in FP64 (lsq_kernel), the IDs in FP32 arithmetic on FP64 data when
+// chi_fact >= 1e-3 (id_batched), FP64 below.
 // The recursion bottom (nodes of at most kDenseSmw unknowns, or L <= 2) forms
 // the node's block from products with unit vectors and inverts it densely.
 #include <cusolverDn.h>
@@ -548,8 +549,9 @@ std::unique_ptr<ProgOp> rbf_build(Ctx& c, LinOp& A, int lam, const std::vector<i
     drank.alloc(sizeof(int32_t) * std::max<size_t>(1, ij.size()));
     upload_vec(dij, ij, c.s);
     const auto t0 = std::chrono::steady_clock::now();
+    // FP32 arithmetic when chi_fact >= 1e-3 (the sketches carry BF16x3 products anyway)
     id_batched(dij.as<IdJob>(), (int)ij.size(), maxn, A64.as<double2>(), dV.as<double2>(), dpiv.as<int32_t>(),
-               drank.as<int32_t>(), c.tol, c.s);
+               drank.as<int32_t>(), c.tol, c.s, /*single=*/c.tol >= 1e-3);
     std::vector<int32_t> piv(poff), rk(ij.size());
     VIE_CUDA(cudaMemcpyAsync(piv.data(), dpiv.p, sizeof(int32_t) * poff, cudaMemcpyDeviceToHost, c.s));
     VIE_CUDA(cudaMemcpyAsync(rk.data(), drank.p, sizeof(int32_t) * ij.size(), cudaMemcpyDeviceToHost, c.s));

@@ -54,9 +54,11 @@ def _refine(h):
 
 
 def test_negative_eps_rcs_converges_under_refinement():
-    """eps = -4 - 0.2j (the paper's value), r = 0.2: halving the pitch brings the RCS closer to Mie
-    (measured: relative RMSE 0.35 at pitch 1/20, 0.29 at 1/40)."""
-    n1, it1, e1 = _refine(1.0 / 20)
-    n2, it2, e2 = _refine(1.0 / 40)
-    print("negative eps refinement: N", n1, "->", n2, "iterations", it1, it2, "RCS relative RMSE", e1, "->", e2)
-    assert e2 < e1
+    """eps = -4 - 0.2j (the paper's value), r = 0.2: each refinement of the pitch (1/20, 1/40,
+    1/60; N = 3,672, 27,360, 89,184) brings the RCS closer to Mie.  The voxel staircase of the
+    surface sets the error of this surface-plasmon response and shrinks slowly with the pitch
+    (reading Q21b), so the test asserts a strictly decreasing error rather than a fixed rate."""
+    res = [_refine(h) for h in (1.0 / 20, 1.0 / 40, 1.0 / 60)]
+    print("negative eps refinement (N, iterations, RCS relative RMSE):", res)
+    e = [r[2] for r in res]
+    assert e[2] < e[1] < e[0]
