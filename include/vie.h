@@ -54,14 +54,18 @@ typedef enum {
 typedef enum { VIE_OP_Z = 0, VIE_OP_ZINV = 1, VIE_OP_ZH = 2, VIE_OP_ZINVH = 3 } vie_opkind;
 typedef enum { VIE_C64 = 0, VIE_C128 = 1 } vie_dtype;
 
-/* Arithmetic of the stored factors and of the multi-RHS applies (spec precision split):
+/* Arithmetic of the stored factors and of the multi-RHS applies:
  *   VIE_P_AUTO       factor_dtype decides; complex FP32 factors apply on the tensor cores from
  *                    16 columns (or the count vie_autotune_rhs chose);
  *   VIE_P_FP64       the plain FP64 method: complex FP64 factors, FP64 applies;
  *   VIE_P_C32        complex FP32 factors and applies, never the tensor cores;
  *   VIE_P_TC_BF16X3  complex FP32 factors, tensor cores (BF16x3 split products, FP32
  *                    accumulation) from 16 columns, crossover fixed;
- *   VIE_P_TC_TF32    a TF32 tensor-core variant: not built (vie_build returns VIE_ENOTSUP). */
+ *   VIE_P_TC_TF32    complex FP32 factors, tensor cores from 16 columns with one TF32
+ *                    product per real product (operands rounded to TF32, 10 mantissa
+ *                    bits; FP32 accumulation): about 1.5x less tensor time than BF16x3
+ *                    at about 5e-4 relative accuracy per product; crossover fixed.
+ *                    The construction of Zinv still runs its products in BF16x3. */
 typedef enum { VIE_P_AUTO = 0, VIE_P_FP64 = 1, VIE_P_C32 = 2, VIE_P_TC_BF16X3 = 3, VIE_P_TC_TF32 = 4 } vie_prec;
 
 /* A scatterer on a cubic voxel lattice of pitch h: voxel (i, j, k) is the cube
@@ -75,6 +79,24 @@ typedef struct {
   const double* eps;
   double h;
 } vie_voxels;
+
+/* A general tetrahedral mesh (Sec. II: the scatterer discretized by tets, one SWG
+ * function per face, Eq. 3).  xyz: host, 3*nv vertex coordinates (lambda0 units);
+ * tet: host, 4*nt vertex ids per tet in any orientation; eps_r: host, 2*nt
+ * (re, im) relative permittivity per tet (finite, nonzero).  Faces are numbered
+ * as the unique sorted vertex-id triples in lexicographic order, T+ of a face is
+ * the lower tet id holding it.  The quadrature tiers of the entries use cells of
+ * pitch h_c = the mean (in tet order) of each tet's shortest edge: a tet's cell
+ * is floor(centroid / h_c), the tier of two elements the Chebyshev distance of
+ * their tets' cells (on a voxel mesh, the voxel rule).  Meant for quasi-uniform
+ * meshes, like those of the paper. */
+typedef struct {
+  int64_t nv;
+  const double* xyz;
+  int64_t nt;
+  const int32_t* tet;
+  const double* eps_r;
+} vie_mesh;
 
 typedef struct {
   double tol_con;      /* chi_con: ID truncation |R_kk| <= tol |R_11| (Eq. 7) */
@@ -123,6 +145,16 @@ typedef struct {
 vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg,
                      void* stream, vie_op** out);
 
+/* vie_build for a general tetrahedral mesh.  The entries are evaluated per element
+ * pair on the fly (no lattice tables): closed-form potentials over the source and
+ * conical rules over the observer in the near tier, conical rules in the mid tier,
+ * 4-point rules in the far tier.  VIE_EINVAL for an empty mesh, a vertex id out of
+ * range, a repeated vertex in a tet, a zero-volume tet, a face shared by more than
+ * two tets, a non-finite coordinate or eps_r, and the configuration errors of
+ * vie_build. */
+vie_status vie_build_mesh(const vie_mesh* mesh, double k0, const vie_config* cfg,
+                          void* stream, vie_op** out);
+
 /* Y = op(X) for op = Z, Zinv, or their adjoints Z^H, Zinv^H (VIE_OP_ZH,
  * VIE_OP_ZINVH: the conjugate-transposed factors in reverse order, the products
  * the randomized construction of Sec. III-B needs; the adjoint factors are
@@ -131,10 +163,25 @@ vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg,
  * with leading dimensions ldx, ldy >= N (in elements), dtype VIE_C64 or
  * VIE_C128 for both.  The factors keep their stored type; accumulation runs
  * in the vector type (c128 vectors give the FP64-accumulated apply used for
- * refinement residuals).  X and Y must not overlap.  (Sec. III-A: "storage
- * and application costs ... O(n log n)"; Algorithm 1 for Zinv.) */
+ * refinement residuals).  X and Y must not overlap.  (Sec. III-A: the
+ * apply of the compressed operator costs O(N log N); Algorithm 1 for Zinv.) */
 vie_status vie_apply(vie_op* op, int32_t which, const void* X, void* Y, int64_t nrhs,
                      int64_t ldx, int64_t ldy, int32_t dtype, void* stream);
+
+/* Grouped apply: Y[i] = op_i(X[i]) for count operators at once, op_i = Z
+ * (which[i] = VIE_OP_Z) or Zinv (VIE_OP_ZINV) of ops[i], each X[i], Y[i] a
+ * device array of complex FP32 (VIE_C64), N_i x nrhs[i] column-major with
+ * leading dimension N_i.  The independent stage chains of the operators (Sec.
+ * III-A; Algorithm 1 for Zinv) run as one launch per stage depth, each a work
+ * list over (operator, factor block, row tile) and, for nrhs[i] at or above the
+ * operator's tensor-core column count, (operator, tensor-core item, 128-column
+ * chunk); the results are bit-identical to count separate vie_apply calls.
+ * Operators need c64 factors, and each may appear once per call (its
+ * workspaces hold that operator's vectors).  Stream-ordered on `stream`.
+ * VIE_EINVAL: null pointers, nrhs < 1, a repeated operator, c128 factors, a
+ * kind other than Z / Zinv; VIE_ENOTSUP: Zinv of an operator without one. */
+vie_status vie_apply_group(vie_op* const* ops, const int32_t* which, const void* const* X,
+                           void* const* Y, const int64_t* nrhs, int32_t count, void* stream);
 
 /* vie_apply that also times each kernel of the apply with CUDA events on
  * `stream` and waits for it: ms (host, cap >= stages + 2) receives the
@@ -202,6 +249,14 @@ vie_status vie_set_tiling(vie_op* op, int32_t which, const int32_t* choice, int3
  * SIMT path (BF16x3 split products, FP32 accumulation). */
 vie_status vie_autotune_rhs(vie_op* op, int32_t which, int32_t* tc_min_rhs, void* stream);
 
+/* Switch the multi-RHS arithmetic of a built operator with complex FP32 factors:
+ * prec = VIE_P_C32 (SIMT only), VIE_P_TC_BF16X3 or VIE_P_TC_TF32 (tensor cores
+ * from 16 columns).  Waits for the device, drops the packed tensor-core tiles and
+ * captured graphs of Z and Zinv (repacked on the next multi-RHS apply) and sets
+ * vie_config.prec.  VIE_EINVAL: null op, another prec value, complex FP64
+ * factors. */
+vie_status vie_set_prec(vie_op* op, int32_t prec);
+
 /* Block shapes of one stage of an apply program (introspection for profiling):
  * *count receives the number of blocks; M[i], K[i] (host, may be NULL) their
  * rows and columns for i < min(count, cap). */
@@ -250,9 +305,10 @@ vie_status vie_farfield(vie_op* op, const void* I, int64_t nrhs, const double* d
 
 /* Face table of the mesh: faces (host 3*N int32, sorted vertex ids, faces
  * sorted lexicographically), tp / tm (host N int32: the lower / higher tet
- * id holding the face, tm = -1 on the boundary).  Vertices are the lattice
- * points sorted lexicographically by (i, j, k); tets are voxel-major, then
- * the 6 axis permutations in lexicographic order.  Any pointer may be NULL. */
+ * id holding the face, tm = -1 on the boundary).  Voxel bodies: vertices are
+ * the lattice points sorted lexicographically by (i, j, k); tets are
+ * voxel-major, then the 6 axis permutations in lexicographic order.  General
+ * meshes: vertices and tets as given.  Any pointer may be NULL. */
 vie_status vie_mesh_faces(const vie_op* op, int32_t* faces, int32_t* tp, int32_t* tm);
 
 /* Host only (no GPU needed): the mesh and cluster tree that vie_build would
@@ -261,6 +317,14 @@ vie_status vie_mesh_faces(const vie_op* op, int32_t* faces, int32_t* tp, int32_t
  * L_H.  Call once with NULL arrays to size them. */
 vie_status vie_mesh_host(const vie_voxels* body, int32_t leaf, int64_t* n, int32_t* faces, int32_t* tp,
                          int32_t* tm, int32_t* perm, int32_t* levels);
+
+/* vie_mesh_host for a general tet mesh (vie_build_mesh's mesh, cells and tree):
+ * additionally cells (host 3*nt int32, NULL allowed) receives the tier cell of
+ * every tet and *cell_pitch (NULL allowed) the cell pitch h_c.  Faces and tree as
+ * in vie_mesh_host (vertex ids as given).  Errors as in vie_build_mesh. */
+vie_status vie_mesh_host_tets(const vie_mesh* mesh, int32_t leaf, int64_t* n, int32_t* faces,
+                              int32_t* tp, int32_t* tm, int32_t* perm, int32_t* levels,
+                              int32_t* cells, double* cell_pitch);
 
 /* perm (host, N int32): original face index at each position of the cluster
  * tree order (Sec. III-A: KD bisection to a complete tree of L_H levels). */
@@ -322,9 +386,13 @@ vie_status vie_wait_selftest(int32_t spins, void* stream);
  * admitted while the device memory of their Krylov state (about
  * N nrhs (restart + 6) 16 bytes) fits `mem_budget`; each vie_server_step
  * admits what fits, advances every admitted request by one preconditioned
- * GMRES iteration (the applies of all columns of one operator batched into
- * one multi-column apply: tensor cores from 16 columns, or the count vie_autotune_rhs chose), ends restart cycles
- * with an FP64 refinement residual, and retires finished requests.
+ * GMRES iteration (the columns of each operator packed into one block, the
+ * blocks of all operators applied in one grouped launch sequence as in
+ * vie_apply_group, tensor cores for a block of 16 columns or the count
+ * vie_autotune_rhs chose, replayed from a CUDA graph while the operators and
+ * column counts of the step repeat), ends restart cycles with an FP64
+ * refinement residual, and retires finished requests.  The operators need c64
+ * factors (VIE_EINVAL otherwise).
  * Requests submitted between steps join at the next step.  All work runs on
  * `stream`; every call is synchronous with respect to the host. */
 typedef struct vie_server vie_server;

@@ -32,6 +32,11 @@ the voxels holding them (a surface element lives in the voxel of its T+):
         tri_conical(3); the smooth remainder g_s = (exp(-j k0 R) - 1)/(4 pi R)
         uses tet_conical(2) / tri_conical(2) on both sides.
   Gram term: tet4 (exact for the quadratic integrand).
+On a general tet mesh (mesh.build_mesh_general) the voxels are replaced by the
+tier cells of mesh.tier_cells, and a pair of elements whose tets share a vertex is
+near (D <= 1) whatever its cells, so touching elements always take the singular
+treatment; on a voxel mesh tets that share a vertex lie in voxels at distance <= 1,
+so the voxel rule is unchanged.
 """
 from __future__ import annotations
 
@@ -161,6 +166,9 @@ class Elements:
         self.face_tri = mesh["verts"][mesh["faces"]]  # (nf, 3, 3)
         self.face_vox = mesh["vox_ijk"][mesh["tet_vox"][fp]]
         self.tet_vox = mesh["vox_ijk"][mesh["tet_vox"]]
+        self.general = bool(np.all(np.asarray(mesh["tet_type"]) < 0))  # general tet mesh: tier cells
+        self.tet_ids = np.asarray(mesh["tets"])
+        self.face_owner = fp
         self.face_area = 0.5 * np.linalg.norm(
             np.cross(self.face_tri[:, 1] - self.face_tri[:, 0], self.face_tri[:, 2] - self.face_tri[:, 0]), axis=1)
 
@@ -180,6 +188,14 @@ class Elements:
 
 def _tier(va, vb):
     return np.abs(va[:, None, :] - vb[None, :, :]).max(-1)
+
+
+def _share_vertex(E, ta, tb, grid: bool):
+    """Whether tets ta and tb share a vertex: for every (ta[i], tb[j]) (grid) or (ta[i], tb[i])."""
+    A, B = E.tet_ids[ta], E.tet_ids[tb]
+    if grid:
+        return (A[:, None, :, None] == B[None, :, None, :]).any((-1, -2))
+    return (A[:, :, None] == B[:, None, :]).any((-1, -2))
 
 
 # ----------------------------------------------------------------------------------
@@ -226,6 +242,8 @@ def tet_pair_blocks(E, to, ts):
     """(len(to), len(ts), 4, 4) contributions of every tet pair to the SWG entries."""
     k0 = E.k0
     tier = _tier(E.tet_vox[to], E.tet_vox[ts])
+    if E.general:
+        tier = np.where(_share_vertex(E, to, ts, grid=True), np.minimum(tier, 1), tier)
     I, J = np.meshgrid(np.arange(len(to)), np.arange(len(ts)), indexing="ij")
     out = np.zeros((len(to), len(ts), 4, 4), dtype=np.complex128)
     div_o = swg_div(E.geo, to)
@@ -327,6 +345,10 @@ def _all_pairs(E, kind_o, eo, kind_s, es, chunk: int = 40000):
     for s in range(0, len(I), chunk):
         a, b = I[s:s + chunk], J[s:s + chunk]
         tier = np.abs(vo[a] - vs[b]).max(1)
+        if E.general:
+            ta = eo[a] if kind_o == "t" else E.face_owner[eo[a]]
+            tb = es[b] if kind_s == "t" else E.face_owner[es[b]]
+            tier = np.where(_share_vertex(E, ta, tb, grid=False), np.minimum(tier, 1), tier)
         out[s:s + chunk] = _pair_scalar(E, kind_o, eo[a], kind_s, es[b], tier)
     return out.reshape(len(eo), len(es))
 

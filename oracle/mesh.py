@@ -121,3 +121,63 @@ def swg_eval(geo: dict, t: np.ndarray, r: np.ndarray) -> np.ndarray:
 def swg_div(geo: dict, t: np.ndarray) -> np.ndarray:
     """Divergence of the 4 SWG functions of tets t: s_a a_a / V, shape (len(t), 4)."""
     return geo["sign"][t] * geo["area"][t] / geo["vol"][t][:, None]
+
+
+def tier_cells(verts: np.ndarray, tets: np.ndarray):
+    """Cell pitch and per-tet cells of the quadrature-tier rule on a general tet mesh.
+
+    Reading of the tier rule beyond voxel meshes (the paper is silent): the cell pitch
+    h_c is the mean over the tets (in id order) of each tet's shortest edge, and tet t
+    lives in cell floor(c_t / h_c) of its centroid c_t = (P0 + P1 + P2 + P3) / 4.  On a
+    voxel/Kuhn mesh the shortest edge of every tet is the voxel pitch and each centroid
+    lies at least h/4 inside its voxel, so the cells are the voxels and the rule is the
+    voxel rule.  Every step is written with +, -, *, / and sqrt in a fixed order (no
+    library reductions), so any implementation that follows it gets the same cells.
+    (The entries also treat any two elements whose tets share a vertex as near; see
+    oracle.entries.)"""
+    P = verts[tets]
+    nt = len(tets)
+    emin = np.full(nt, np.inf)
+    for a in range(4):
+        for b in range(a + 1, 4):
+            d = P[:, b] - P[:, a]
+            emin = np.minimum(emin, np.sqrt((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]))
+    s = 0.0
+    for v in emin.tolist():  # sequential sum in tet order
+        s += v
+    hc = s / nt
+    c = (((P[:, 0] + P[:, 1]) + P[:, 2]) + P[:, 3]) * 0.25
+    return hc, np.floor(c / hc).astype(np.int64)
+
+
+def build_mesh_general(verts, tets, eps) -> dict:
+    """SWG face table of a general tetrahedral mesh (Sec. II, Eq. 3): vertices (nv, 3),
+    tets (nt, 4) vertex ids in any orientation, eps (nt,) complex relative permittivity
+    per tet.  Numbering as in ``build_mesh``: vertices and tets as given; faces are the
+    unique sorted vertex-id triples sorted lexicographically; T+ is the lower tet id
+    holding a face; local face a is opposite local vertex a.  The quadrature tiers use
+    the cells of ``tier_cells`` in place of voxels."""
+    verts = np.asarray(verts, dtype=np.float64)
+    tets = np.asarray(tets, dtype=np.int64)
+    nt = len(tets)
+    hc, cells = tier_cells(verts, tets)
+    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    tri = np.sort(tets[:, loc], axis=2).reshape(-1, 3)
+    faces, finv = np.unique(tri, axis=0, return_inverse=True)
+    finv = finv.reshape(nt, 4)
+    nf = len(faces)
+    tp = np.full(nf, -1, dtype=np.int64)
+    tm = np.full(nf, -1, dtype=np.int64)
+    lp = np.full(nf, -1, dtype=np.int64)
+    lm = np.full(nf, -1, dtype=np.int64)
+    for t in range(nt):
+        for a in range(4):
+            f = finv[t, a]
+            if tp[f] < 0:
+                tp[f], lp[f] = t, a
+            else:
+                assert tm[f] < 0, "a face is shared by at most two tets"
+                tm[f], lm[f] = t, a
+    return dict(h=hc, verts=verts, tets=tets, tet_vox=np.arange(nt), tet_type=np.full(nt, -1),
+                vox_ijk=cells, eps=np.asarray(eps, dtype=np.complex128), faces=faces, face_tp=tp,
+                face_tm=tm, face_lp=lp, face_lm=lm, tet_faces=finv)

@@ -27,7 +27,8 @@ VIE_P_AUTO, VIE_P_FP64, VIE_P_C32, VIE_P_TC_BF16X3, VIE_P_TC_TF32 = 0, 1, 2, 3, 
 EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "vie_program_info", "vie_program_blocks", "vie_autotune", "vie_autotune_rhs", "vie_set_tiling", "vie_entries", "vie_rhs_planewave", "vie_solve", "vie_solve_tfqmr", "vie_farfield",
            "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_wait_selftest", "vie_destroy", "vie_last_error",
            "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy",
-           "vie_save", "vie_load", "vie_shard_range", "vie_apply_shard"]
+           "vie_save", "vie_load", "vie_shard_range", "vie_apply_shard", "vie_apply_group", "vie_build_mesh",
+           "vie_mesh_host_tets", "vie_set_prec"]
 
 
 class VieError(RuntimeError):
@@ -38,6 +39,19 @@ class VieError(RuntimeError):
 
 class _Voxels(ctypes.Structure):
     _fields_ = [("nvox", ctypes.c_int64), ("ijk", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("h", ctypes.c_double)]
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("nt", ctypes.c_int64), ("tet", ctypes.c_void_p),
+                ("eps_r", ctypes.c_void_p)]
+
+
+def _tetmesh(mesh):
+    """vie_mesh of a workloads.TetMesh-like object (verts, tets, eps); returns (struct, arrays kept alive)."""
+    xyz = np.ascontiguousarray(mesh.verts, dtype=np.float64)
+    tet = np.ascontiguousarray(mesh.tets, dtype=np.int32)
+    eps = np.ascontiguousarray(np.stack([np.real(mesh.eps), np.imag(mesh.eps)], 1), dtype=np.float64)
+    return _Mesh(len(xyz), xyz.ctypes.data, len(tet), tet.ctypes.data, eps.ctypes.data), (xyz, tet, eps)
 
 
 class _Config(ctypes.Structure):
@@ -102,6 +116,10 @@ def load_library(path: str = LIB_PATH):
         "vie_shard_range": [P, I32, I32, P, P],
         "vie_apply_shard": [P, I32, I32, I32, P, P, I64, I64, I64, I32, P],
         "vie_load": [ctypes.c_char_p, P, P],
+        "vie_apply_group": [P, P, P, P, P, I32, P],
+        "vie_build_mesh": [P, D, P, P, P],
+        "vie_mesh_host_tets": [P, I32, P, P, P, P, P, P, P, P],
+        "vie_set_prec": [P, I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -172,21 +190,49 @@ def mesh_host(body, leaf: int = 64):
     return dict(faces=f, tp=tp, tm=tm, perm=perm, levels=lev.value)
 
 
+def mesh_host_tets(mesh, leaf: int = 64):
+    """Face table, tier cells and cluster-tree permutation of a general tet mesh (host only)."""
+    lib = load_library()
+    mm, keep = _tetmesh(mesh)
+    n = ctypes.c_int64(0)
+    _check(lib.vie_mesh_host_tets(ctypes.byref(mm), leaf, ctypes.byref(n), None, None, None, None, None, None, None))
+    N = n.value
+    f = np.zeros((N, 3), dtype=np.int32)
+    tp = np.zeros(N, dtype=np.int32)
+    tm = np.zeros(N, dtype=np.int32)
+    perm = np.zeros(N, dtype=np.int32)
+    cells = np.zeros((len(mesh.tets), 3), dtype=np.int32)
+    lev = ctypes.c_int32(0)
+    hc = ctypes.c_double(0)
+    _check(lib.vie_mesh_host_tets(ctypes.byref(mm), leaf, ctypes.byref(n), f.ctypes.data, tp.ctypes.data,
+                                  tm.ctypes.data, perm.ctypes.data, ctypes.byref(lev), cells.ctypes.data,
+                                  ctypes.byref(hc)))
+    return dict(faces=f, tp=tp, tm=tm, perm=perm, levels=lev.value, cells=cells, cell_pitch=hc.value)
+
+
 class Operator:
-    """A HOD-BF compressed VIE operator Z (and Zinv) resident on the current GPU."""
+    """A HOD-BF compressed VIE operator Z (and Zinv) resident on the current GPU.
+
+    ``body`` is a voxel body (``ijk``, ``eps``, ``h``: vie_build) or a general tetrahedral
+    mesh (``verts``, ``tets``, ``eps`` per tet: vie_build_mesh)."""
 
     def __init__(self, body, k0: float, tol_con: float = 1e-4, tol_fact: float = 0.0, leaf: int = 64,
                  factor_dtype: str = "c64", seed: int = 1, oversample: int = 10, id_tol_div: int = 1,
                  inv_dense_max: int = 0, prec: int = 0, stream=None):
         lib = load_library()
         self._h = ctypes.c_void_p()
-        ijk = np.ascontiguousarray(body.ijk, dtype=np.int32)
-        eps = np.ascontiguousarray(np.stack([np.real(body.eps), np.imag(body.eps)], 1), dtype=np.float64)
-        vox = _Voxels(len(ijk), ijk.ctypes.data, eps.ctypes.data, float(body.h))
         cfg = _Config(tol_con, tol_fact, leaf, VIE_C64 if factor_dtype == "c64" else VIE_C128, seed, oversample,
                       id_tol_div, inv_dense_max, prec)
-        _check(lib.vie_build(ctypes.byref(vox), float(k0), ctypes.byref(cfg), _stream_ptr(stream),
-                             ctypes.byref(self._h)))
+        if hasattr(body, "tets"):
+            mm, keep = _tetmesh(body)
+            _check(lib.vie_build_mesh(ctypes.byref(mm), float(k0), ctypes.byref(cfg), _stream_ptr(stream),
+                                      ctypes.byref(self._h)))
+        else:
+            ijk = np.ascontiguousarray(body.ijk, dtype=np.int32)
+            eps = np.ascontiguousarray(np.stack([np.real(body.eps), np.imag(body.eps)], 1), dtype=np.float64)
+            vox = _Voxels(len(ijk), ijk.ctypes.data, eps.ctypes.data, float(body.h))
+            _check(lib.vie_build(ctypes.byref(vox), float(k0), ctypes.byref(cfg), _stream_ptr(stream),
+                                 ctypes.byref(self._h)))
         self.stats = self.get_stats()
         self.n = int(self.stats.n)
 
@@ -216,6 +262,10 @@ class Operator:
                                     ctypes.c_void_p(Yc.data_ptr()), nrhs, ldx, ldy, _dtype_code(Xc),
                                     _stream_ptr(stream)))
         return Y
+
+    def set_prec(self, prec: int):
+        """Switch the multi-RHS arithmetic (VIE_P_C32, VIE_P_TC_BF16X3, VIE_P_TC_TF32) of c64 factors."""
+        _check(_lib.vie_set_prec(self._h, prec))
 
     def save(self, path: str, stream=None):
         _check(_lib.vie_save(self._h, os.fsencode(path), _stream_ptr(stream)))
@@ -494,3 +544,28 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def apply_group(jobs, stream=None):
+    """Grouped apply (``vie_apply_group``): ``jobs`` is a list of (Operator, X, op) with op
+    VIE_OP_Z or VIE_OP_ZINV and X a complex64 CUDA tensor (N,) or (N, nrhs); the independent
+    applies run as one launch per stage depth.  Returns the list of results (same shapes)."""
+    import torch
+
+    n = len(jobs)
+    outs, keep = [], []
+    ops = (ctypes.c_void_p * max(1, n))()
+    which = (ctypes.c_int32 * max(1, n))()
+    xs = (ctypes.c_void_p * max(1, n))()
+    ys = (ctypes.c_void_p * max(1, n))()
+    nr = (ctypes.c_int64 * max(1, n))()
+    for i, (opr, X, kind) in enumerate(jobs):
+        assert X.dtype == torch.complex64, "grouped applies take complex64 vectors"
+        Xc, nrhs, ldx = _colmajor(X, opr.n)
+        assert ldx == opr.n, "grouped applies take X with leading dimension N"
+        Y = torch.empty((nrhs, opr.n), dtype=X.dtype, device=X.device).t()
+        keep.append(Xc)
+        outs.append(Y[:, 0] if X.dim() == 1 else Y)
+        ops[i], which[i], xs[i], ys[i], nr[i] = opr._h.value, kind, Xc.data_ptr(), Y.data_ptr(), nrhs
+    _check(_lib.vie_apply_group(ops, which, xs, ys, nr, n, _stream_ptr(stream)))
+    return outs

@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3,-ffp-contract=off", "--expt-relaxed-constexpr"]
-SOURCES = ["host.cpp", "api.cpp", "entries.cu", "id.cu", "build.cu", "apply.cu", "solve.cu", "inverse.cu", "noalloc.cu", "tc.cu", "serve.cu", "program.cu", "randinv.cu", "io.cpp", "shard.cu"]
+SOURCES = ["host.cpp", "api.cpp", "entries.cu", "id.cu", "build.cu", "apply.cu", "solve.cu", "inverse.cu", "noalloc.cu", "tc.cu", "serve.cu", "program.cu", "randinv.cu", "io.cpp", "shard.cu", "group.cu"]
 
 
 def _compile(src: str) -> str:

@@ -102,71 +102,94 @@ extern "C" {
 
 const char* vie_last_error(void) { return g_err.c_str(); }
 
+static void check_config(const vie_config* cfg, double k0) {
+  VIE_REQUIRE(cfg->leaf >= 4 && cfg->tol_con > 0 && k0 > 0, VIE_EINVAL, "invalid configuration");
+  VIE_REQUIRE(cfg->factor_dtype == VIE_C64 || cfg->factor_dtype == VIE_C128, VIE_EINVAL, "factor dtype");
+  VIE_REQUIRE(cfg->prec >= VIE_P_AUTO && cfg->prec <= VIE_P_TC_TF32, VIE_EINVAL, "bad precision");
+}
+
+// everything after the mesh: geometry, cluster tree, Z (Sec. III-A), Zinv (Sec. III-B)
+static void build_operator(vie_op* h, double k0, const vie_config* cfg, cudaStream_t s, double t0) {
+  h->cfg = *cfg;
+  if (h->cfg.oversample <= 0) h->cfg.oversample = 10;
+  if (cfg->prec == VIE_P_FP64) h->cfg.factor_dtype = VIE_C128;
+  if (cfg->prec == VIE_P_C32 || cfg->prec == VIE_P_TC_BF16X3 || cfg->prec == VIE_P_TC_TF32)
+    h->cfg.factor_dtype = VIE_C64;
+  geometry_upload(h->mesh, k0, h->geo, s);
+  if (!h->mesh.general) geometry_table(h->geo, s);
+  const int64_t N = h->mesh.nf;
+  build_tree(face_centroids(h->mesh), cfg->leaf, h->tree);
+  h->perm.alloc(sizeof(int32_t) * N);
+  VIE_CUDA(cudaMemcpyAsync(h->perm.p, h->tree.perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+  h->tet_faces.alloc(sizeof(int32_t) * 4 * h->mesh.nt);
+  VIE_CUDA(cudaMemcpyAsync(h->tet_faces.p, h->mesh.tet_faces.data(), sizeof(int32_t) * 4 * h->mesh.nt,
+                           cudaMemcpyHostToDevice, s));
+  BuildResult br;
+  build_hodbf(h, s, br);
+  const int never = 1 << 30;
+  h->z.tc_min_rhs = h->zinv.tc_min_rhs = cfg->prec == VIE_P_C32 ? never : kTcMinRhs;
+  VIE_CUDA(cudaStreamSynchronize(s));
+  h->stats.n = N;
+  h->stats.ntets = h->mesh.nt;
+  h->stats.levels = h->tree.levels;
+  h->stats.max_rank = br.max_rank;
+  h->stats.entries_z = h->z.entries;
+  h->stats.bytes_z = h->z.bytes;
+  h->stats.entries_evaluated = br.entries_evaluated;
+  h->stats.apply_stages_z = (int32_t)h->z.stages.size();
+  h->stats.build_entries_seconds = br.t_entries;
+  h->stats.build_id_seconds = br.t_id;
+  h->stats.build_host_seconds = br.t_host;
+  h->stats.build_seconds = now_s() - t0;
+  if (cfg->tol_fact > 0) {
+    double t1 = now_s();
+    BuildResult bi;
+    build_inverse(h, s, bi);
+    VIE_CUDA(cudaStreamSynchronize(s));
+    h->stats.entries_zinv = h->zinv.entries;
+    h->stats.bytes_zinv = h->zinv.bytes;
+    h->stats.apply_stages_zinv = (int32_t)h->zinv.stages.size();
+    h->stats.max_rank = std::max(h->stats.max_rank, bi.max_rank);
+    h->stats.invert_seconds = now_s() - t1;
+    h->stats.zinv_top_level = h->zinv_top_level;
+  }
+  // the TF32 variant serves the caller's applies; the construction above ran its
+  // products with the BF16x3 split
+  if (cfg->prec == VIE_P_TC_TF32) {
+    program_set_tc_variant(h->z, true);
+    program_set_tc_variant(h->zinv, true);
+  }
+}
+
 vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg, void* stream, vie_op** out) {
   return guarded([&] {
     VIE_REQUIRE(body && cfg && out, VIE_EINVAL, "null argument");
     VIE_REQUIRE(body->nvox > 0 && body->ijk && body->eps && body->h > 0, VIE_EINVAL, "empty or invalid voxel body");
-    VIE_REQUIRE(cfg->leaf >= 4 && cfg->tol_con > 0 && k0 > 0, VIE_EINVAL, "invalid configuration");
-    VIE_REQUIRE(cfg->factor_dtype == VIE_C64 || cfg->factor_dtype == VIE_C128, VIE_EINVAL, "factor dtype");
-    VIE_REQUIRE(cfg->prec >= VIE_P_AUTO && cfg->prec <= VIE_P_TC_TF32, VIE_EINVAL, "bad precision");
-    VIE_REQUIRE(cfg->prec != VIE_P_TC_TF32, VIE_ENOTSUP, "the TF32 tensor-core variant is not built");
+    check_config(cfg, k0);
     *out = nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
-    double t0 = now_s();
+    const double t0 = now_s();
     vie_op* h = new vie_op();
     try {
-      h->cfg = *cfg;
-      if (h->cfg.oversample <= 0) h->cfg.oversample = 10;
-      if (cfg->prec == VIE_P_FP64) h->cfg.factor_dtype = VIE_C128;
-      if (cfg->prec == VIE_P_C32 || cfg->prec == VIE_P_TC_BF16X3) h->cfg.factor_dtype = VIE_C64;
       build_mesh(*body, h->mesh);
-      geometry_upload(h->mesh, k0, h->geo, s);
-      geometry_table(h->geo, s);
-      // face centroids and cluster tree
-      const int64_t N = h->mesh.nf;
-      std::vector<double> pts(3 * N);
-      for (int64_t f = 0; f < N; ++f)
-        for (int d = 0; d < 3; ++d) {
-          double a = double(h->mesh.vlat[3 * h->mesh.faces[3 * f] + d]) * h->mesh.h;
-          double b = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 1] + d]) * h->mesh.h;
-          double c = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 2] + d]) * h->mesh.h;
-          pts[3 * f + d] = ((a + b) + c) / 3.0;
-        }
-      build_tree(pts, cfg->leaf, h->tree);
-      h->perm.alloc(sizeof(int32_t) * N);
-      VIE_CUDA(cudaMemcpyAsync(h->perm.p, h->tree.perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
-      h->tet_faces.alloc(sizeof(int32_t) * 4 * h->mesh.nt);
-      VIE_CUDA(cudaMemcpyAsync(h->tet_faces.p, h->mesh.tet_faces.data(), sizeof(int32_t) * 4 * h->mesh.nt,
-                               cudaMemcpyHostToDevice, s));
-      BuildResult br;
-      build_hodbf(h, s, br);
-      const int never = 1 << 30;
-      h->z.tc_min_rhs = h->zinv.tc_min_rhs = cfg->prec == VIE_P_C32 ? never : kTcMinRhs;
-      VIE_CUDA(cudaStreamSynchronize(s));
-      h->stats.n = N;
-      h->stats.ntets = h->mesh.nt;
-      h->stats.levels = h->tree.levels;
-      h->stats.max_rank = br.max_rank;
-      h->stats.entries_z = h->z.entries;
-      h->stats.bytes_z = h->z.bytes;
-      h->stats.entries_evaluated = br.entries_evaluated;
-      h->stats.apply_stages_z = (int32_t)h->z.stages.size();
-      h->stats.build_entries_seconds = br.t_entries;
-      h->stats.build_id_seconds = br.t_id;
-      h->stats.build_host_seconds = br.t_host;
-      h->stats.build_seconds = now_s() - t0;
-      if (cfg->tol_fact > 0) {
-        double t1 = now_s();
-        BuildResult bi;
-        build_inverse(h, s, bi);
-        VIE_CUDA(cudaStreamSynchronize(s));
-        h->stats.entries_zinv = h->zinv.entries;
-        h->stats.bytes_zinv = h->zinv.bytes;
-        h->stats.apply_stages_zinv = (int32_t)h->zinv.stages.size();
-        h->stats.max_rank = std::max(h->stats.max_rank, bi.max_rank);
-        h->stats.invert_seconds = now_s() - t1;
-        h->stats.zinv_top_level = h->zinv_top_level;
-      }
+      build_operator(h, k0, cfg, (cudaStream_t)stream, t0);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+vie_status vie_build_mesh(const vie_mesh* mesh, double k0, const vie_config* cfg, void* stream, vie_op** out) {
+  return guarded([&] {
+    VIE_REQUIRE(mesh && cfg && out, VIE_EINVAL, "null argument");
+    check_config(cfg, k0);
+    *out = nullptr;
+    const double t0 = now_s();
+    vie_op* h = new vie_op();
+    try {
+      build_mesh_general(*mesh, h->mesh);
+      build_operator(h, k0, cfg, (cudaStream_t)stream, t0);
     } catch (...) {
       delete h;
       throw;
@@ -194,7 +217,11 @@ vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t n
       const bool inv = which == VIE_OP_ZINVH;
       Program& a = inv ? h->zinvh : h->zh;
       bool& ready = inv ? h->zinvh_ready : h->zh_ready;
-      if (!ready) { program_adjoint(inv ? h->zinv : h->z, a, s); ready = true; }
+      if (!ready) {
+        program_adjoint(inv ? h->zinv : h->z, a, s);
+        program_set_tc_variant(a, (inv ? h->zinv : h->z).tc_tf32);
+        ready = true;
+      }
       if (nrhs >= a.tc_min_rhs && dtype == VIE_C64) program_prepare_tc(a, s);
       ensure_ws(h, a, nrhs, dtype);
       program_apply_adjoint(a, h->perm.as<int32_t>(), X, Y, nrhs, ldx, ldy, dtype, h->xt.p, h->yt.p, h->coef.p, s);
@@ -286,7 +313,8 @@ vie_status vie_autotune(vie_op* h, int32_t which, int32_t* choice, int32_t cap, 
 
 vie_status vie_autotune_rhs(vie_op* h, int32_t which, int32_t* tc_min_rhs, void* stream) {
   return guarded([&] {
-    if (h && (h->cfg.prec == VIE_P_C32 || h->cfg.prec == VIE_P_TC_BF16X3)) {  // the precision fixes the path
+    if (h && (h->cfg.prec == VIE_P_C32 || h->cfg.prec == VIE_P_TC_BF16X3 ||
+              h->cfg.prec == VIE_P_TC_TF32)) {  // the precision fixes the path
       Program& p = which == VIE_OP_ZINV ? h->zinv : h->z;
       if (tc_min_rhs) *tc_min_rhs = p.tc_min_rhs;
       return;
@@ -300,6 +328,21 @@ vie_status vie_autotune_rhs(vie_op* h, int32_t which, int32_t* tc_min_rhs, void*
     VIE_CUDA(cudaMemsetAsync(h->coef.p, 0, h->coef.bytes, (cudaStream_t)stream));
     const int m = program_tune_rhs(p, h->xt.p, h->yt.p, h->coef.p, (cudaStream_t)stream);
     if (tc_min_rhs) *tc_min_rhs = m;
+  });
+}
+
+vie_status vie_set_prec(vie_op* h, int32_t prec) {
+  return guarded([&] {
+    VIE_REQUIRE(h, VIE_EINVAL, "null operator");
+    VIE_REQUIRE(prec == VIE_P_C32 || prec == VIE_P_TC_BF16X3 || prec == VIE_P_TC_TF32, VIE_EINVAL,
+                "prec must be VIE_P_C32, VIE_P_TC_BF16X3 or VIE_P_TC_TF32");
+    VIE_REQUIRE(h->z.factor_dtype == VIE_C64, VIE_EINVAL, "the operator has complex FP64 factors");
+    const int never = 1 << 30;
+    for (Program* p : {&h->z, &h->zinv, &h->zh, &h->zinvh}) {
+      program_set_tc_variant(*p, prec == VIE_P_TC_TF32);
+      p->tc_min_rhs = prec == VIE_P_C32 ? never : kTcMinRhs;
+    }
+    h->cfg.prec = prec;
   });
 }
 
@@ -358,16 +401,30 @@ vie_status vie_mesh_host(const vie_voxels* body, int32_t leaf, int64_t* n, int32
     if (tp) std::memcpy(tp, m.tp.data(), sizeof(int32_t) * m.nf);
     if (tm) std::memcpy(tm, m.tm.data(), sizeof(int32_t) * m.nf);
     if (perm || levels) {
-      std::vector<double> pts(3 * m.nf);
-      for (int64_t f = 0; f < m.nf; ++f)
-        for (int d = 0; d < 3; ++d) {
-          double a = double(m.vlat[3 * m.faces[3 * f] + d]) * m.h;
-          double b = double(m.vlat[3 * m.faces[3 * f + 1] + d]) * m.h;
-          double c = double(m.vlat[3 * m.faces[3 * f + 2] + d]) * m.h;
-          pts[3 * f + d] = ((a + b) + c) / 3.0;
-        }
+      const std::vector<double> pts = face_centroids(m);
       Tree t;
       build_tree(pts, leaf, t);
+      if (perm) std::memcpy(perm, t.perm.data(), sizeof(int32_t) * m.nf);
+      if (levels) *levels = t.levels;
+    }
+  });
+}
+
+vie_status vie_mesh_host_tets(const vie_mesh* mesh, int32_t leaf, int64_t* n, int32_t* faces, int32_t* tp,
+                              int32_t* tm, int32_t* perm, int32_t* levels, int32_t* cells, double* cell_pitch) {
+  return guarded([&] {
+    VIE_REQUIRE(mesh && n && leaf >= 4, VIE_EINVAL, "null argument or leaf < 4");
+    Mesh m;
+    build_mesh_general(*mesh, m);
+    *n = m.nf;
+    if (faces) std::memcpy(faces, m.faces.data(), sizeof(int32_t) * 3 * m.nf);
+    if (tp) std::memcpy(tp, m.tp.data(), sizeof(int32_t) * m.nf);
+    if (tm) std::memcpy(tm, m.tm.data(), sizeof(int32_t) * m.nf);
+    if (cells) std::memcpy(cells, m.cells.data(), sizeof(int32_t) * 3 * m.nt);
+    if (cell_pitch) *cell_pitch = m.h;
+    if (perm || levels) {
+      Tree t;
+      build_tree(face_centroids(m), leaf, t);
       if (perm) std::memcpy(perm, t.perm.data(), sizeof(int32_t) * m.nf);
       if (levels) *levels = t.levels;
     }

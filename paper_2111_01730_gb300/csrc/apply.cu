@@ -373,6 +373,99 @@ __global__ void __launch_bounds__(256) stage_kernel(const OpDesc* __restrict__ o
   }
 }
 
+// Grouped SIMT stage: the tiles of one stage of several operators (SimtGroup), any
+// column count, in chunks of eight columns with the last chunk masked.  Per column
+// the arithmetic is that of stage1_kernel / stage_kernel on the same tiles (same
+// lanes per row, the same sequence of fused multiply-adds over k, the same shuffle
+// tree), so a grouped apply returns the bits of the per-operator applies.
+__global__ void __launch_bounds__(256) group_simt_kernel(const __grid_constant__ SimtGroup grp) {
+  constexpr int NR = 8, U = 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp0; t < grp.total; t += nwarps) {
+    int si = 0;  // the segment (operator) of tile t
+    while (si + 1 < grp.n && grp.s[si + 1].begin <= t) ++si;
+    const SimtSeg& sg = grp.s[si];
+    const Tile tl = sg.tiles[t - sg.begin];
+    const OpDesc op = sg.ops[tl.op];
+    const int nrhs = sg.nrhs, K = op.K;
+    const int g = tl.g, rp = 32 / g;
+    const int li = lane & (g - 1);
+    const float2* xin = (op.in_space == SP_X ? sg.xt : (op.in_space == SP_Y ? (const float2*)sg.yt : sg.coef)) +
+                        op.in_off * nrhs;
+    float2* yout = (op.out_space == SP_Y ? sg.yt : (op.out_space == SP_X ? const_cast<float2*>(sg.xt) : sg.coef)) +
+                   op.out_off * nrhs;
+    for (int c0 = 0; c0 < nrhs; c0 += NR) {
+      const int nc = min(NR, nrhs - c0);  // uniform across the warp
+      for (int r = tl.r0 + lane / g; r < tl.r0 + tl.nr; r += rp) {
+        const bool active = r < op.M;
+        float re[NR], im[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) { re[j] = 0.f; im[j] = 0.f; }
+        if (active) {
+          const float4* row = reinterpret_cast<const float4*>(sg.mats + op.mat_off + (int64_t)r * op.ld);
+          for (int k0 = 2 * li; k0 < K; k0 += 2 * U * g) {
+            float4 a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int k = k0 + 2 * g * u;
+              a[u] = k < K ? __ldcs(row + (k >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int k = k0 + 2 * g * u;
+              if (k < K) {
+                const float2* x0 = xin + (int64_t)k * nrhs + c0;
+                const bool two = k + 1 < K;
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                  if (j < nc) {
+                    const float2 v0 = __ldg(x0 + j);
+                    const float2 v1 = two ? __ldg(x0 + nrhs + j) : make_float2(0.f, 0.f);
+                    re[j] = fmaf(a[u].x, v0.x, re[j]); re[j] = fmaf(-a[u].y, v0.y, re[j]);
+                    im[j] = fmaf(a[u].x, v0.y, im[j]); im[j] = fmaf(a[u].y, v0.x, im[j]);
+                    re[j] = fmaf(a[u].z, v1.x, re[j]); re[j] = fmaf(-a[u].w, v1.y, re[j]);
+                    im[j] = fmaf(a[u].z, v1.y, im[j]); im[j] = fmaf(a[u].w, v1.x, im[j]);
+                  }
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+          if (j < nc)
+            for (int o = g >> 1; o > 0; o >>= 1) {
+              re[j] += __shfl_xor_sync(0xffffffffu, re[j], o);
+              im[j] += __shfl_xor_sync(0xffffffffu, im[j], o);
+            }
+        if (active && li == 0) {
+          float2* yr = yout + (int64_t)r * nrhs + c0;
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            if (j < nc) {
+              if (op.accumulate) {
+                const float2 v = yr[j];
+                yr[j] = make_float2(v.x + re[j], v.y + im[j]);
+              } else {
+                yr[j] = make_float2(re[j], im[j]);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+void simt_launch_group(const SimtGroup& g, cudaStream_t s) {
+  if (g.total == 0) return;
+  const int grid = (int)std::min<int64_t>((g.total + 7) / 8, 152 * 16);
+  group_simt_kernel<<<grid, 256, 0, s>>>(g);
+  VIE_CUDA(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------
 // permutation gather / scatter (cluster-tree order <-> original face order)
 // ---------------------------------------------------------------------------
@@ -751,8 +844,22 @@ void program_prepare_tc(Program& p, cudaStream_t s) {
   if (p.tc_ready || p.factor_dtype != VIE_C64) return;
   // keep an existing flag: graphs captured earlier (single-RHS bulk stages) hold its address
   ensure_err(p, s);
-  for (Stage& st : p.stages) tc_prepare_stage(st, st.host_ops, s);
+  for (Stage& st : p.stages) tc_prepare_stage(st, st.host_ops, p.tc_tf32, s);
   p.tc_ready = true;
+}
+
+void program_set_tc_variant(Program& p, bool tf32) {
+  if (p.tc_tf32 == tf32) return;
+  VIE_CUDA(cudaDeviceSynchronize());  // nothing in flight may still read the tiles
+  for (auto& g : p.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  p.graphs.clear();
+  for (Stage& st : p.stages) {
+    st.tc_tiles.release(); st.tc_ops.release(); st.rest_ops.release(); st.rest_tiles.release();
+    st.tc_items = st.tc_bytes = st.rest_ntiles = 0;
+  }
+  p.tc_ready = false;
+  p.tc_tf32 = tf32;
 }
 
 int64_t program_launches(const Program& p, int64_t nrhs, int dtype) {

@@ -218,14 +218,8 @@ void build_program(vie_op* h, const std::vector<BfSpec>& specs, EntrySource& src
   const vie_config& cfg = h->cfg;
   const int elem_bytes = cfg.factor_dtype == VIE_C64 ? 8 : 16;
   // face centroids (original order), same arithmetic as the tree
-  std::vector<double> pts(3 * N);
-  for (int64_t f = 0; f < N; ++f)
-    for (int d = 0; d < 3; ++d) {
-      double a = double(h->mesh.vlat[3 * h->mesh.faces[3 * f] + d]) * h->mesh.h;
-      double b = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 1] + d]) * h->mesh.h;
-      double c = double(h->mesh.vlat[3 * h->mesh.faces[3 * f + 2] + d]) * h->mesh.h;
-      pts[3 * f + d] = ((a + b) + c) / 3.0;
-    }
+  const std::vector<double> pts = face_centroids(h->mesh);
+  (void)N;
   Sampler smp{t, pts, LH, cfg.seed, cfg.oversample};
   // butterflies
   std::vector<BF> bfs;

@@ -24,6 +24,9 @@
 //         conical(2) on both sides.
 #include <math.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include "internal.h"
 
 namespace vie {
@@ -255,9 +258,11 @@ __global__ void table_kernel(Tab* tab, double h, double k0) {
 // ---------------------------------------------------------------------------
 struct EntryCtx {
   const FaceDev* faces;
-  const TetDev* tets;
-  const Tab* tab;
+  const TetDev* tets;   // general meshes: vx, vy, vz hold the tet's tier cell
+  const Tab* tab;       // voxel meshes only
+  const TetGeo* geo;    // general meshes only
   double h, k0;
+  int general;
 };
 
 __device__ __forceinline__ const Tab* tab_lookup(const EntryCtx& c, int p, int q, int dx, int dy, int dz) {
@@ -437,11 +442,266 @@ __device__ double2 entry(const EntryCtx& c, int m, int n) {
   return z;
 }
 
+// ---------------------------------------------------------------------------
+// general tetrahedral meshes: every element pair integrated on the fly with the
+// same quadrature specification as the lattice tables (tiers from the tets'
+// cells), the vertices taken from the tet's own geometry record
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ V3 gvert(const TetGeo& g, int a) { return v3(g.P[a][0], g.P[a][1], g.P[a][2]); }
+
+// point i of the level-`level` rule over the tet (face < 0) or its local face `face`;
+// face rules run over the face's vertices in increasing global vertex id
+__device__ V3 grule_point(const TetGeo& g, int face, int level, int i, double& w) {
+  V3 r = v3(0, 0, 0);
+  if (face < 0) {
+    const double* row = level == 0 ? c_tet4[i] : (level == 2 ? c_tetc2[i] : c_tetc3[i]);
+    for (int a = 0; a < 4; ++a) r = r + row[a] * gvert(g, a);
+    w = row[4] * g.vol;
+    return r;
+  }
+  const double* row = level == 0 ? c_tri3[i] : (level == 2 ? c_tric2[i] : c_tric3[i]);
+  for (int a = 0; a < 3; ++a) r = r + row[a] * gvert(g, g.fv[face][a]);
+  w = row[3] * g.area[face];
+  return r;
+}
+
+// U = int_T 1/R dv', W = int_T (r'-r)/R dv' over a general tet
+__device__ void gtet_pot(V3 r, const TetGeo& g, double& U, V3& W) {
+  U = 0.0;
+  W = v3(0, 0, 0);
+  for (int f = 0; f < 4; ++f) {
+    const V3 A = gvert(g, g.fv[f][0]), B = gvert(g, g.fv[f][1]), C = gvert(g, g.fv[f][2]);
+    const V3 nf = v3(g.nrm[f][0], g.nrm[f][1], g.nrm[f][2]);
+    const double hf = dot(A - r, nf);
+    double im1, i1;
+    tri_pot(r, A, B, C, im1, i1);
+    if (fabs(hf) > 0.0) U += 0.5 * hf * im1;
+    W = W + i1 * nf;
+  }
+}
+
+// tier of two elements held by tets T and Tp: Chebyshev distance of the tets' cells,
+// at most 1 (near) when the tets share a vertex
+__device__ __forceinline__ int gtier(const EntryCtx& c, int T, int Tp) {
+  const TetDev a = c.tets[T], b = c.tets[Tp];
+  int tier = max(abs(b.vx - a.vx), max(abs(b.vy - a.vy), abs(b.vz - a.vz)));
+  if (tier > 1) {
+    const TetGeo& ga = c.geo[T];
+    const TetGeo& gb = c.geo[Tp];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j)
+        if (ga.vid[i] == gb.vid[j]) tier = 1;
+  }
+  return tier;
+}
+
+// far tier in FP32 for the builder: tet4 x tet4, coordinates relative to the observer
+// tet's first vertex (formed in FP64), FP32 kernel evaluations
+__device__ void gfar_tet_pair_f32(const TetGeo& gA, const TetGeo& gB, V3 qa, V3 qb, double k0, double2& sum,
+                                  double2& sumv) {
+  const V3 o = gvert(gA, 0);
+  float sr = 0.f, si = 0.f, vr = 0.f, vi = 0.f;
+  F3 rj[4];
+  float wj[4];
+  for (int j = 0; j < 4; ++j) {
+    V3 r = v3(0, 0, 0);
+    for (int a = 0; a < 4; ++a) r = r + c_tet4[j][a] * (gvert(gB, a) - o);
+    rj[j] = F3{(float)r.x, (float)r.y, (float)r.z};
+    wj[j] = (float)(c_tet4[j][4] * gB.vol);
+  }
+  const V3 qar = qa - o, qbr = qb - o;
+  for (int i = 0; i < 4; ++i) {
+    V3 r = v3(0, 0, 0);
+    for (int a = 0; a < 4; ++a) r = r + c_tet4[i][a] * (gvert(gA, a) - o);
+    const F3 ri{(float)r.x, (float)r.y, (float)r.z};
+    const float wi = (float)(c_tet4[i][4] * gA.vol);
+    const float ax = ri.x - (float)qar.x, ay = ri.y - (float)qar.y, az = ri.z - (float)qar.z;
+    for (int j = 0; j < 4; ++j) {
+      const float ex = ri.x - rj[j].x, ey = ri.y - rj[j].y, ez = ri.z - rj[j].z;
+      const float R = sqrtf(ex * ex + ey * ey + ez * ez);
+      float sn, cs;
+      sincosf((float)k0 * R, &sn, &cs);
+      const float f = (float)kInv4Pi * wi * wj[j] / R;
+      const float gr = cs * f, gi = -sn * f;
+      sr += gr;
+      si += gi;
+      const float d = ax * (rj[j].x - (float)qbr.x) + ay * (rj[j].y - (float)qbr.y) + az * (rj[j].z - (float)qbr.z);
+      vr += gr * d;
+      vi += gi * d;
+    }
+  }
+  sum = make_double2(sr, si);
+  sumv = make_double2(vr, vi);
+}
+
+// contribution of the tet pair (T, a) x (T', b) to Z(m, n) on a general mesh:
+// A = int int g (r - q_a).(r' - q_b), Phi = int int g
+template <bool FAR32>
+__device__ double2 gtet_pair(const EntryCtx& c, int T, int a, double sa, int Tp, int b, double sb) {
+  const TetDev tA = c.tets[T], tB = c.tets[Tp];
+  const TetGeo& gA = c.geo[T];
+  const TetGeo& gB = c.geo[Tp];
+  const double ca = sa * gA.area[a] / (3.0 * gA.vol), cb = sb * gB.area[b] / (3.0 * gB.vol);
+  const double diva = 3.0 * ca, divb = 3.0 * cb;
+  const V3 qa = gvert(gA, a), qb = gvert(gB, b);
+  const int tier = gtier(c, T, Tp);
+  double2 A = make_double2(0, 0), Phi = make_double2(0, 0);
+  if (tier <= 1) {
+    // 1/(4 pi R): closed form over the source tet, conical(3) over the observer
+    for (int i = 0; i < 27; ++i) {
+      double wi;
+      const V3 ri = grule_point(gA, -1, 3, i, wi);
+      double U;
+      V3 W;
+      gtet_pot(ri, gB, U, W);
+      const double cw = wi * kInv4Pi;
+      Phi.x += cw * U;
+      A.x += cw * dot(ri - qa, W + U * (ri - qb));  // int (r' - q_b)/R = W + U (r - q_b)
+    }
+    // smooth remainder: conical(2) on both sides
+    for (int i = 0; i < 8; ++i) {
+      double wi;
+      const V3 ri = grule_point(gA, -1, 2, i, wi);
+      for (int j = 0; j < 8; ++j) {
+        double wj;
+        const V3 rj = grule_point(gB, -1, 2, j, wj);
+        const double2 g = cscale(green_smooth(norm(ri - rj), c.k0), wi * wj);
+        Phi = cadd(Phi, g);
+        A = cadd(A, cscale(g, dot(ri - qa, rj - qb)));
+      }
+    }
+  } else if (tier == 2) {
+    for (int i = 0; i < 8; ++i) {
+      double wi;
+      const V3 ri = grule_point(gA, -1, 2, i, wi);
+      for (int j = 0; j < 8; ++j) {
+        double wj;
+        const V3 rj = grule_point(gB, -1, 2, j, wj);
+        const double2 g = cscale(green(norm(ri - rj), c.k0), wi * wj);
+        Phi = cadd(Phi, g);
+        A = cadd(A, cscale(g, dot(ri - qa, rj - qb)));
+      }
+    }
+  } else if (FAR32) {
+    gfar_tet_pair_f32(gA, gB, qa, qb, c.k0, Phi, A);
+  } else {
+    for (int i = 0; i < 4; ++i) {
+      double wi;
+      const V3 ri = grule_point(gA, -1, 0, i, wi);
+      for (int j = 0; j < 4; ++j) {
+        double wj;
+        const V3 rj = grule_point(gB, -1, 0, j, wj);
+        const double2 g = cscale(green(norm(ri - rj), c.k0), wi * wj);
+        Phi = cadd(Phi, g);
+        A = cadd(A, cscale(g, dot(ri - qa, rj - qb)));
+      }
+    }
+  }
+  const double2 kap = make_double2(tB.kap_re, tB.kap_im);
+  const double k2 = c.k0 * c.k0, cab = ca * cb;
+  double2 z = cmul(kap, make_double2(-k2 * cab * A.x + diva * divb * Phi.x, -k2 * cab * A.y + diva * divb * Phi.y));
+  if (T == Tp) {  // Gram term, tet4 (exact for the quadratic integrand)
+    double g = 0.0;
+    for (int i = 0; i < 4; ++i) {
+      double wi;
+      const V3 ri = grule_point(gA, -1, 0, i, wi);
+      g += wi * dot(ri - qa, ri - qb);
+    }
+    z = cadd(z, cscale(make_double2(tA.inveps_re, tA.inveps_im), g * cab));
+  }
+  return z;
+}
+
+// scalar int int g between element fa of tet T (observer) and element fb of tet Tp
+__device__ double2 gpair_scalar(const EntryCtx& c, int T, int fa, int Tp, int fb) {
+  const TetGeo& gA = c.geo[T];
+  const TetGeo& gB = c.geo[Tp];
+  const int tier = gtier(c, T, Tp);
+  const int nA2 = fa < 0 ? 8 : 4, nB2 = fb < 0 ? 8 : 4;
+  double2 S = make_double2(0, 0);
+  if (tier <= 1) {
+    for (int i = 0; i < (fa < 0 ? 27 : 9); ++i) {
+      double wi;
+      const V3 ri = grule_point(gA, fa, 3, i, wi);
+      double pot;
+      if (fb < 0) {
+        V3 W;
+        gtet_pot(ri, gB, pot, W);
+      } else {
+        double i1;
+        tri_pot(ri, gvert(gB, gB.fv[fb][0]), gvert(gB, gB.fv[fb][1]), gvert(gB, gB.fv[fb][2]), pot, i1);
+      }
+      S.x += wi * pot * kInv4Pi;
+    }
+    for (int i = 0; i < nA2; ++i) {
+      double wi;
+      const V3 ri = grule_point(gA, fa, 2, i, wi);
+      for (int j = 0; j < nB2; ++j) {
+        double wj;
+        const V3 rj = grule_point(gB, fb, 2, j, wj);
+        S = cadd(S, cscale(green_smooth(norm(ri - rj), c.k0), wi * wj));
+      }
+    }
+    return S;
+  }
+  const int lvl = tier == 2 ? 2 : 0;
+  const int nA = rule_size(fa, lvl), nB = rule_size(fb, lvl);
+  for (int i = 0; i < nA; ++i) {
+    double wi;
+    const V3 ri = grule_point(gA, fa, lvl, i, wi);
+    for (int j = 0; j < nB; ++j) {
+      double wj;
+      const V3 rj = grule_point(gB, fb, lvl, j, wj);
+      S = cadd(S, cscale(green(norm(ri - rj), c.k0), wi * wj));
+    }
+  }
+  return S;
+}
+
+template <bool FAR32>
+__device__ double2 gentry(const EntryCtx& c, int m, int n) {
+  const FaceDev Fm = c.faces[m], Fn = c.faces[n];
+  double2 z = make_double2(0, 0);
+  const int Tm[2] = {Fm.tp, Fm.tm}, Am[2] = {Fm.lp, Fm.lm};
+  const int Tn[2] = {Fn.tp, Fn.tm}, Bn[2] = {Fn.lp, Fn.lm};
+  for (int i = 0; i < 2; ++i) {
+    if (Tm[i] < 0) continue;
+    for (int j = 0; j < 2; ++j) {
+      if (Tn[j] < 0) continue;
+      z = cadd(z, gtet_pair<FAR32>(c, Tm[i], Am[i], i == 0 ? 1.0 : -1.0, Tn[j], Bn[j], j == 0 ? 1.0 : -1.0));
+    }
+  }
+  const double2 jump = make_double2(Fn.jump_re, Fn.jump_im);
+  const bool has_jump = (jump.x != 0.0 || jump.y != 0.0);
+  if (Fm.boundary) {
+    for (int j = 0; j < 2; ++j) {
+      if (Tn[j] < 0) continue;
+      const TetDev tB = c.tets[Tn[j]];
+      const double divb = (j == 0 ? 1.0 : -1.0) * c.geo[Tn[j]].area[Bn[j]] / c.geo[Tn[j]].vol;
+      const double2 s = gpair_scalar(c, Fm.tp, Fm.lp, Tn[j], -1);
+      z = cadd(z, cscale(cmul(make_double2(tB.kap_re, tB.kap_im), s), -divb));
+    }
+  }
+  if (has_jump) {
+    for (int i = 0; i < 2; ++i) {
+      if (Tm[i] < 0) continue;
+      const double diva = (i == 0 ? 1.0 : -1.0) * c.geo[Tm[i]].area[Am[i]] / c.geo[Tm[i]].vol;
+      const double2 s = gpair_scalar(c, Tm[i], -1, Fn.tp, Fn.lp);
+      z = cadd(z, cscale(cmul(jump, s), diva));
+    }
+    if (Fm.boundary) {
+      const double2 s = gpair_scalar(c, Fm.tp, Fm.lp, Fn.tp, Fn.lp);
+      z = cadd(z, cscale(cmul(jump, s), -1.0));
+    }
+  }
+  return z;
+}
+
 template <bool FAR32>
 __global__ void entries_pairs_kernel(EntryCtx c, const int32_t* rows, const int32_t* cols, int64_t count,
                                      double2* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = entry<FAR32>(c, rows[i], cols[i]);
+    out[i] = c.general ? gentry<FAR32>(c, rows[i], cols[i]) : entry<FAR32>(c, rows[i], cols[i]);
 }
 
 template <bool FAR32>
@@ -456,7 +716,8 @@ __global__ void entries_blocks_kernel(EntryCtx c, const EntryBlock* blocks, cons
     const EntryBlock b = blocks[lo];
     int64_t k = g - prefix[lo];
     int i = int(k % b.m), j = int(k / b.m);
-    out[b.out_off + k] = entry<FAR32>(c, rows[b.row_off + i], cols[b.col_off + j]);
+    const int m = rows[b.row_off + i], n = cols[b.col_off + j];
+    out[b.out_off + k] = c.general ? gentry<FAR32>(c, m, n) : entry<FAR32>(c, m, n);
   }
 }
 
@@ -474,6 +735,21 @@ __global__ void rhs_kernel(EntryCtx c, int64_t n, const double* khat, const doub
     const int T[2] = {F.tp, F.tm}, A[2] = {F.lp, F.lm};
     for (int s = 0; s < 2; ++s) {
       if (T[s] < 0) continue;
+      if (c.general) {  // conical(3) over the tet, absolute coordinates
+        const TetGeo& G = c.geo[T[s]];
+        const double ca = (s == 0 ? 1.0 : -1.0) * G.area[A[s]] / (3.0 * G.vol);
+        const V3 qa = gvert(G, A[s]);
+        for (int i = 0; i < 27; ++i) {
+          double w;
+          const V3 r = grule_point(G, -1, 3, i, w);
+          double sn, cs;
+          sincos(-c.k0 * dot(kh, r), &sn, &cs);
+          const double f = w * ca * dot(r - qa, pl);
+          acc.x += f * cs;
+          acc.y += f * sn;
+        }
+        continue;
+      }
       const TetDev t = c.tets[T[s]];
       const double h = c.h, vol = h * h * h / 6.0;
       const double ca = (s == 0 ? 1.0 : -1.0) * c_area[t.type][A[s]] * h * h / (3.0 * vol);
@@ -503,6 +779,32 @@ __global__ void farfield_kernel(EntryCtx c, int64_t nt, const int32_t* tet_faces
   const double h = c.h, vol = h * h * h / 6.0;
   for (int64_t T = threadIdx.x; T < nt; T += blockDim.x) {
     const TetDev t = c.tets[T];
+    if (c.general) {
+      const TetGeo& G = c.geo[T];
+      double2 coef[4];
+      double ca[4];
+      for (int a = 0; a < 4; ++a) {
+        const int f = tet_faces[4 * T + a];
+        coef[a] = I[f + (int64_t)r * n];
+        ca[a] = (c.faces[f].tp == T ? 1.0 : -1.0) * G.area[a] / (3.0 * G.vol);
+      }
+      for (int i = 0; i < 27; ++i) {
+        double w;
+        const V3 rg = grule_point(G, -1, 3, i, w);
+        double2 d[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+        for (int a = 0; a < 4; ++a) {
+          const V3 f = ca[a] * (rg - gvert(G, a));
+          d[0] = cadd(d[0], cscale(coef[a], f.x));
+          d[1] = cadd(d[1], cscale(coef[a], f.y));
+          d[2] = cadd(d[2], cscale(coef[a], f.z));
+        }
+        double sn, cs;
+        sincos(c.k0 * dot(u, rg), &sn, &cs);
+        const double2 ph = cmul(make_double2(cs, sn), make_double2(t.kap_re * w, t.kap_im * w));
+        for (int k = 0; k < 3; ++k) acc[k] = cadd(acc[k], cmul(ph, d[k]));
+      }
+      continue;
+    }
     Elem E{t.type, -1, 0, 0, 0};
     double2 coef[4];
     V3 qa[4];
@@ -595,13 +897,18 @@ void geometry_upload(const Mesh& m, double k0, Geometry& g, cudaStream_t s) {
   g.nt = m.nt;
   g.h = m.h;
   g.k0 = k0;
+  g.general = m.general;
   std::vector<TetDev> tets(m.nt);
-  std::vector<double> kap(2 * m.nt);
   for (int64_t t = 0; t < m.nt; ++t) {
-    int64_t v = t / 6;
+    const int64_t v = m.general ? t : t / 6;  // row of eps: the voxel, or the tet itself
     TetDev d;
-    d.vx = m.vox[3 * v]; d.vy = m.vox[3 * v + 1]; d.vz = m.vox[3 * v + 2];
-    d.type = int(t % 6);
+    if (m.general) {
+      d.vx = m.cells[3 * t]; d.vy = m.cells[3 * t + 1]; d.vz = m.cells[3 * t + 2];
+      d.type = -1;
+    } else {
+      d.vx = m.vox[3 * v]; d.vy = m.vox[3 * v + 1]; d.vz = m.vox[3 * v + 2];
+      d.type = int(t % 6);
+    }
     double er = m.eps[2 * v], ei = m.eps[2 * v + 1];
     double den = er * er + ei * ei;
     d.inveps_re = er / den;
@@ -622,6 +929,42 @@ void geometry_upload(const Mesh& m, double k0, Geometry& g, cudaStream_t s) {
     d.jump_im = kmi - kpi;
     faces[f] = d;
   }
+  if (m.general) {  // per-tet geometry records: vertices, volume, face areas and outward normals
+    static const int loc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+    std::vector<TetGeo> geo(m.nt);
+    for (int64_t t = 0; t < m.nt; ++t) {
+      TetGeo G{};
+      const int32_t* T = &m.tets[4 * t];
+      for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 3; ++d) G.P[a][d] = m.xyz[3 * T[a] + d];
+      double e[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 3; ++d) e[a][d] = G.P[a + 1][d] - G.P[0][d];
+      const double cx = e[0][1] * e[1][2] - e[0][2] * e[1][1], cy = e[0][2] * e[1][0] - e[0][0] * e[1][2],
+                   cz = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+      G.vol = std::abs(cx * e[2][0] + cy * e[2][1] + cz * e[2][2]) / 6.0;
+      for (int a = 0; a < 4; ++a) {
+        const double* A = G.P[loc[a][0]];
+        const double* B = G.P[loc[a][1]];
+        const double* C = G.P[loc[a][2]];
+        const double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]}, w[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+        const double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double ln = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        const double sg =
+            (n[0] * (A[0] - G.P[a][0]) + n[1] * (A[1] - G.P[a][1]) + n[2] * (A[2] - G.P[a][2])) > 0 ? 1.0 : -1.0;
+        for (int d = 0; d < 3; ++d) G.nrm[a][d] = sg * n[d] / ln;
+        G.area[a] = 0.5 * ln;
+        int lv[3] = {loc[a][0], loc[a][1], loc[a][2]};
+        std::sort(lv, lv + 3, [&](int x, int y) { return T[x] < T[y]; });
+        for (int k = 0; k < 3; ++k) G.fv[a][k] = (int8_t)lv[k];
+        G.vid[a] = T[a];
+      }
+      geo[t] = G;
+    }
+    g.geo.alloc(sizeof(TetGeo) * m.nt);
+    VIE_CUDA(cudaMemcpyAsync(g.geo.p, geo.data(), sizeof(TetGeo) * m.nt, cudaMemcpyHostToDevice, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+  }
   g.tets.alloc(sizeof(TetDev) * m.nt);
   g.faces.alloc(sizeof(FaceDev) * m.nf);
   VIE_CUDA(cudaMemcpyAsync(g.tets.p, tets.data(), sizeof(TetDev) * m.nt, cudaMemcpyHostToDevice, s));
@@ -637,7 +980,8 @@ void geometry_table(Geometry& g, cudaStream_t s) {
 }
 
 static EntryCtx ctx(const Geometry& g) {
-  return EntryCtx{g.faces.as<FaceDev>(), g.tets.as<TetDev>(), g.table.as<Tab>(), g.h, g.k0};
+  return EntryCtx{g.faces.as<FaceDev>(), g.tets.as<TetDev>(), g.table.as<Tab>(), g.geo.as<TetGeo>(),
+                  g.h,               g.k0,                   g.general ? 1 : 0};
 }
 
 void entries_pairs(const Geometry& g, const int32_t* rows, const int32_t* cols, int64_t count, double2* out,

@@ -25,6 +25,8 @@ static inline uint64_t pack_lattice(int64_t i, int64_t j, int64_t k) {
   return (uint64_t(i + B) << 42) | (uint64_t(j + B) << 21) | uint64_t(k + B);
 }
 
+static void make_face_table(Mesh& m);
+
 void build_mesh(const vie_voxels& body, Mesh& m) {
   m.h = body.h;
   m.nvox = body.nvox;
@@ -56,7 +58,12 @@ void build_mesh(const vie_voxels& body, Mesh& m) {
   m.tets.resize(4 * m.nt);
   for (int64_t i = 0; i < 4 * m.nt; ++i)
     m.tets[i] = int32_t(std::lower_bound(uniq.begin(), uniq.end(), keys[i]) - uniq.begin());
-  // faces: local face a is opposite local vertex a; unique sorted triples, lexicographic
+  make_face_table(m);
+}
+
+// faces: local face a is opposite local vertex a; unique sorted triples, lexicographic;
+// T+ = the lower tet id holding the face
+static void make_face_table(Mesh& m) {
   struct Rec { std::array<int32_t, 3> v; int32_t t; int32_t a; };
   std::vector<Rec> recs(4 * m.nt);
   static const int loc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
@@ -75,7 +82,7 @@ void build_mesh(const vie_voxels& body, Mesh& m) {
   for (size_t i = 0; i < recs.size();) {
     size_t j = i + 1;
     while (j < recs.size() && recs[j].v == recs[i].v) ++j;
-    VIE_REQUIRE(j - i <= 2, VIE_EINVAL, "non-manifold face (duplicate voxels?)");
+    VIE_REQUIRE(j - i <= 2, VIE_EINVAL, "non-manifold face (shared by more than two tets)");
     int32_t f = (int32_t)m.tp.size();
     m.faces.insert(m.faces.end(), recs[i].v.begin(), recs[i].v.end());
     m.tp.push_back(recs[i].t); m.lp.push_back(recs[i].a);
@@ -89,6 +96,86 @@ void build_mesh(const vie_voxels& body, Mesh& m) {
     i = j;
   }
   m.nf = (int64_t)m.tp.size();
+}
+
+// General tetrahedral mesh (Sec. II): vertices and tets as given, the face table as for
+// voxel meshes, and the tier cells of the quadrature rule: the cell pitch is the mean
+// (in tet order) of each tet's shortest edge, a tet's cell is floor(centroid / pitch).
+// On a voxel/Kuhn mesh the cells are the voxels.  Every step uses +, -, *, / and sqrt
+// in a fixed order, so the cells do not depend on the machine.
+void build_mesh_general(const vie_mesh& mm, Mesh& m) {
+  VIE_REQUIRE(mm.nv >= 4 && mm.nt >= 1 && mm.xyz && mm.tet && mm.eps_r, VIE_EINVAL, "empty or invalid tet mesh");
+  VIE_REQUIRE(mm.nv < (int64_t(1) << 31) && mm.nt < (int64_t(1) << 29), VIE_EINVAL, "tet mesh too large");
+  m.general = true;
+  m.nv = mm.nv;
+  m.nt = mm.nt;
+  m.nvox = 0;
+  m.xyz.assign(mm.xyz, mm.xyz + 3 * mm.nv);
+  m.tets.assign(mm.tet, mm.tet + 4 * mm.nt);
+  m.eps.assign(mm.eps_r, mm.eps_r + 2 * mm.nt);
+  for (double v : m.xyz) VIE_REQUIRE(std::isfinite(v), VIE_EINVAL, "vertex coordinate not finite");
+  for (int64_t t = 0; t < m.nt; ++t) {
+    const int32_t* T = &m.tets[4 * t];
+    for (int a = 0; a < 4; ++a) {
+      VIE_REQUIRE(T[a] >= 0 && T[a] < m.nv, VIE_EINVAL, "tet vertex id out of range");
+      for (int b = 0; b < a; ++b) VIE_REQUIRE(T[a] != T[b], VIE_EINVAL, "tet with a repeated vertex");
+    }
+    const double* P0 = &m.xyz[3 * T[0]];
+    double e[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) e[a][d] = m.xyz[3 * T[a + 1] + d] - P0[d];
+    const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                       e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                       e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    VIE_REQUIRE(std::abs(det) > 0.0 && std::isfinite(det), VIE_EINVAL, "degenerate tet (zero volume)");
+    VIE_REQUIRE(std::isfinite(m.eps[2 * t]) && std::isfinite(m.eps[2 * t + 1]) &&
+                    (m.eps[2 * t] != 0.0 || m.eps[2 * t + 1] != 0.0),
+                VIE_EINVAL, "eps_r must be finite and nonzero");
+  }
+  double sum = 0.0;
+  for (int64_t t = 0; t < m.nt; ++t) {
+    const int32_t* T = &m.tets[4 * t];
+    double emin = INFINITY;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        const double dx = m.xyz[3 * T[b]] - m.xyz[3 * T[a]];
+        const double dy = m.xyz[3 * T[b] + 1] - m.xyz[3 * T[a] + 1];
+        const double dz = m.xyz[3 * T[b] + 2] - m.xyz[3 * T[a] + 2];
+        emin = std::min(emin, std::sqrt((dx * dx + dy * dy) + dz * dz));
+      }
+    sum += emin;
+  }
+  m.h = sum / double(m.nt);
+  m.cells.resize(3 * m.nt);
+  for (int64_t t = 0; t < m.nt; ++t) {
+    const int32_t* T = &m.tets[4 * t];
+    for (int d = 0; d < 3; ++d) {
+      const double c = (((m.xyz[3 * T[0] + d] + m.xyz[3 * T[1] + d]) + m.xyz[3 * T[2] + d]) + m.xyz[3 * T[3] + d]) * 0.25;
+      const double q = std::floor(c / m.h);
+      VIE_REQUIRE(std::abs(q) < double(1 << 30), VIE_EINVAL, "tet far from the origin for its size");
+      m.cells[3 * t + d] = (int32_t)q;
+    }
+  }
+  make_face_table(m);
+}
+
+std::vector<double> face_centroids(const Mesh& m) {
+  std::vector<double> pts(3 * m.nf);
+  for (int64_t f = 0; f < m.nf; ++f)
+    for (int d = 0; d < 3; ++d) {
+      double a, b, c;
+      if (m.general) {
+        a = m.xyz[3 * m.faces[3 * f] + d];
+        b = m.xyz[3 * m.faces[3 * f + 1] + d];
+        c = m.xyz[3 * m.faces[3 * f + 2] + d];
+      } else {
+        a = double(m.vlat[3 * m.faces[3 * f] + d]) * m.h;
+        b = double(m.vlat[3 * m.faces[3 * f + 1] + d]) * m.h;
+        c = double(m.vlat[3 * m.faces[3 * f + 2] + d]) * m.h;
+      }
+      pts[3 * f + d] = ((a + b) + c) / 3.0;
+    }
+  return pts;
 }
 
 // ---------------------------------------------------------------------------

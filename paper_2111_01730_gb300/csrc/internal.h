@@ -66,17 +66,22 @@ struct DevBuf {
 // mesh (host): voxels -> Kuhn tets -> faces (SWG table), Sec. II / Eq. (3)
 // ---------------------------------------------------------------------------
 struct Mesh {
-  double h = 0;
+  double h = 0;                    // voxel pitch; general meshes: the tier-cell pitch
   int64_t nvox = 0, nt = 0, nf = 0, nv = 0;
+  bool general = false;            // built from a vie_mesh (vertex coordinates, any tets)
   std::vector<int32_t> vox;        // 3*nvox
-  std::vector<double> eps;         // 2*nvox
+  std::vector<double> eps;         // 2*nvox (voxel meshes) or 2*nt (general meshes)
   std::vector<int32_t> tets;       // 4*nt vertex ids
-  std::vector<int32_t> vlat;       // 3*nv lattice coordinates of the vertices
+  std::vector<int32_t> vlat;       // 3*nv lattice coordinates of the vertices (voxel meshes)
+  std::vector<double> xyz;         // 3*nv vertex coordinates (general meshes)
+  std::vector<int32_t> cells;      // 3*nt tier cells of the tets (general meshes)
   std::vector<int32_t> faces;      // 3*nf sorted vertex ids
   std::vector<int32_t> tp, tm, lp, lm;  // nf: T+, T-, local face index in T+ / T-
   std::vector<int32_t> tet_faces;  // 4*nt
 };
 void build_mesh(const vie_voxels& body, Mesh& m);
+void build_mesh_general(const vie_mesh& mesh, Mesh& m);
+std::vector<double> face_centroids(const Mesh& m);  // 3*nf, ((a + b) + c) / 3 per coordinate
 
 // Kuhn tetrahedra: offsets of the 4 vertices of the 6 types from the voxel corner.
 extern const int kKuhn[6][4][3];
@@ -117,18 +122,30 @@ struct FaceDev {
 };
 
 struct TetDev {
-  int32_t vx, vy, vz;  // voxel
-  int32_t type;        // Kuhn type 0..5
+  int32_t vx, vy, vz;  // voxel (general meshes: the tier cell)
+  int32_t type;        // Kuhn type 0..5 (general meshes: -1)
   double kap_re, kap_im;      // kappa
   double inveps_re, inveps_im;
+};
+
+struct TetGeo {        // a tet of a general mesh
+  double P[4][3];      // vertices in the mesh's order
+  double vol;
+  double area[4];      // area of local face a (opposite vertex a)
+  double nrm[4][3];    // outward unit normal of local face a
+  int8_t fv[4][3];     // local vertices of face a in increasing global vertex id
+  int8_t pad[4];
+  int32_t vid[4];      // global vertex ids (tets sharing one are near)
 };
 
 struct Geometry {
   int64_t n = 0, nt = 0;
   double h = 0, k0 = 0;
+  bool general = false;
   DevBuf faces;   // FaceDev[n]
   DevBuf tets;    // TetDev[nt]
-  DevBuf table;   // near / mid tier interaction table (FP64)
+  DevBuf table;   // near / mid tier interaction table (FP64), voxel meshes
+  DevBuf geo;     // TetGeo[nt], general meshes
 };
 void geometry_upload(const Mesh& m, double k0, Geometry& g, cudaStream_t s);
 void geometry_table(Geometry& g, cudaStream_t s);   // computes the near/mid table
@@ -216,6 +233,7 @@ struct Stage {
   // tensor-core (multi-RHS) form, prepared on first use
   DevBuf tc_tiles, tc_ops, rest_ops, rest_tiles;
   int64_t tc_items = 0, tc_bytes = 0, rest_ntiles = 0;
+  bool tc_tf32 = false;  // tiles packed for the TF32 variant (else BF16x3)
 };
 
 struct Program {         // one operator's apply: gather, stages, scatter
@@ -225,6 +243,7 @@ struct Program {         // one operator's apply: gather, stages, scatter
   int64_t entries = 0, bytes = 0;
   bool tc_ready = false;
   int tc_min_rhs = kTcMinRhs;  // applies with at least this many columns use the tensor cores
+  bool tc_tf32 = false;        // tensor-core variant: TF32 (VIE_P_TC_TF32) or BF16x3
   DevBuf err;            // device int: a bounded wait in a tensor-core kernel ran out
   // CUDA graphs of the stage launches (the gather and scatter stay outside: they
   // touch the caller's X and Y), one per (nrhs, dtype, path, workspaces), least
@@ -250,10 +269,60 @@ struct Program {         // one operator's apply: gather, stages, scatter
   }
 };
 
+// Grouped launches (group.cu): one launch runs the work of one stage of up to
+// kGroupMax operators, each with its own factors, vectors and column count.  The
+// segment table travels in the kernel's parameters (no upload, graph-capturable);
+// a work index finds its segment by a scan over the segments' first indices.
+constexpr int kGroupMax = 16;
+struct SimtSeg {         // SIMT tiles of one operator's stage
+  const OpDesc* ops;
+  const Tile* tiles;
+  const float2* mats;
+  const float2* xt;
+  float2* yt;
+  float2* coef;
+  int64_t begin;         // first global tile index of the segment
+  int32_t nrhs, pad;
+};
+struct SimtGroup {
+  SimtSeg s[kGroupMax];
+  int64_t total;         // tiles of all segments
+  int32_t n, pad;
+};
+struct TcSeg2 {          // tensor-core items of one operator's stage
+  const TcItem* items;
+  const uint8_t* btiles;
+  const float2* xt;
+  float2* yt;
+  float2* coef;
+  int* err;              // set when a bounded wait of this segment's work ran out
+  int64_t begin;         // first global work index (items x 128-column chunks)
+  int32_t nitems, nrhs;
+};
+struct TcGroup {
+  TcSeg2 s[kGroupMax];
+  int64_t total;
+  int32_t n, tf32;       // every segment of a launch has tiles of the same variant
+};
+void simt_launch_group(const SimtGroup& g, cudaStream_t s);
+struct Program;
+struct GroupJob {        // one operator's stages in a grouped apply, on tree-ordered work vectors
+  const Program* p;
+  int64_t nrhs;
+  float2* xt;
+  float2* yt;
+  float2* coef;
+};
+// stage d of every job in launch d (c64 factors and vectors); tensor-core items for
+// jobs with at least the program's tensor-core column count (prepared beforehand)
+void group_run_stages(const std::vector<GroupJob>& jobs, cudaStream_t s);
+
 // tensor-core multi-RHS path (tc.cu)
 bool tc_eligible(const OpDesc& o);
-void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, cudaStream_t s);
+void tc_prepare_stage(Stage& st, const std::vector<OpDesc>& ops, bool tf32, cudaStream_t s);
 void tc_launch(const Stage& st, const void* xt, void* yt, void* coef, int nrhs, int* d_err, cudaStream_t s);
+void tc_launch_group(const TcGroup& g, cudaStream_t s);
+int64_t tc_work_units(int64_t items, int nrhs);  // work indices of a segment: items x 128-column chunks
 size_t tc_smem_bytes();
 void wait_timeout_check(uint32_t spins, int* d_status, cudaStream_t s);
 constexpr size_t kGraphCache = 8;
@@ -285,6 +354,8 @@ void program_apply_graph(Program& p, const int32_t* d_perm, const void* X, void*
                          int64_t ldy, int dtype, void* d_xt, void* d_yt, void* d_c, cudaStream_t s);
 int64_t program_launches(const Program& p, int64_t nrhs, int dtype);
 void program_prepare_tc(Program& p, cudaStream_t s);
+// switch the tensor-core variant; drops the prepared tiles and the captured graphs
+void program_set_tc_variant(Program& p, bool tf32);
 int program_autotune(Program& p, void* xt, void* yt, void* coef, cudaStream_t s, int32_t* choice);
 void program_set_tiling(Program& p, const int32_t* choice, int n, cudaStream_t s);
 int program_tune_rhs(Program& p, void* xt, void* yt, void* coef, cudaStream_t s);

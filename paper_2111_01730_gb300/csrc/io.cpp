@@ -10,8 +10,10 @@
 // operator are bit-identical to applies of the saved one.
 //
 // Layout (little-endian, native struct layout of this library):
-//   "VIEOPv1\0", vie_config, double k0, double h, int64 nvox, int32 ijk[3 nvox],
-//   double eps[2 nvox], vie_stats_t, int32 has_zinv, int32 zinv_top_level,
+//   "VIEOPv1\0", vie_config, double k0, double h, then the body: int64 nvox,
+//   int32 ijk[3 nvox], double eps[2 nvox] (voxels), or int64 -1, int64 nv,
+//   double xyz[3 nv], int64 nt, int32 tet[4 nt], double eps[2 nt] (a tet mesh);
+//   vie_stats_t, int32 has_zinv, int32 zinv_top_level,
 //   int32 tc_min_rhs(Z), int32 tc_min_rhs(Zinv), then each program:
 //   int64 n, ncoef, entries, bytes; int32 factor_dtype, nstages; per stage:
 //   int64 nops, ntiles, mats_bytes, entries, bytes; int32 kernel, pad;
@@ -127,9 +129,18 @@ extern "C" vie_status vie_save(const vie_op* h, const char* path, void* stream) 
     wrv(f, h->cfg);
     wrv(f, h->geo.k0);
     wrv(f, h->mesh.h);
-    wrv(f, h->mesh.nvox);
-    wr(f, h->mesh.vox.data(), sizeof(int32_t) * h->mesh.vox.size());
-    wr(f, h->mesh.eps.data(), sizeof(double) * h->mesh.eps.size());
+    if (h->mesh.general) {  // body: -1, then the tet mesh as given
+      wrv<int64_t>(f, -1);
+      wrv(f, h->mesh.nv);
+      wr(f, h->mesh.xyz.data(), sizeof(double) * h->mesh.xyz.size());
+      wrv(f, h->mesh.nt);
+      wr(f, h->mesh.tets.data(), sizeof(int32_t) * h->mesh.tets.size());
+      wr(f, h->mesh.eps.data(), sizeof(double) * h->mesh.eps.size());
+    } else {
+      wrv(f, h->mesh.nvox);
+      wr(f, h->mesh.vox.data(), sizeof(int32_t) * h->mesh.vox.size());
+      wr(f, h->mesh.eps.data(), sizeof(double) * h->mesh.eps.size());
+    }
     wrv(f, h->stats);
     wrv<int32_t>(f, h->has_zinv ? 1 : 0);
     wrv<int32_t>(f, h->zinv_top_level);
@@ -165,25 +176,35 @@ extern "C" vie_status vie_load(const char* path, void* stream, vie_op** out) {
     h->cfg = rdv<vie_config>(f);
     const double k0 = rdv<double>(f), hh = rdv<double>(f);
     const int64_t nvox = rdv<int64_t>(f);
-    VIE_REQUIRE(nvox > 0 && nvox < (int64_t(1) << 34) && hh > 0 && k0 > 0, VIE_EINVAL, "vie_load: bad body header");
-    std::vector<int32_t> ijk(3 * nvox);
-    std::vector<double> eps(2 * nvox);
-    rd(f, ijk.data(), sizeof(int32_t) * ijk.size());
-    rd(f, eps.data(), sizeof(double) * eps.size());
-    const vie_voxels body{nvox, ijk.data(), eps.data(), hh};
+    VIE_REQUIRE((nvox > 0 || nvox == -1) && nvox < (int64_t(1) << 34) && hh > 0 && k0 > 0, VIE_EINVAL,
+                "vie_load: bad body header");
     // mesh, tree and interaction tables remade from the inputs (deterministic host code)
-    build_mesh(body, h->mesh);
-    geometry_upload(h->mesh, k0, h->geo, s);
-    geometry_table(h->geo, s);
+    if (nvox == -1) {
+      const int64_t nv = rdv<int64_t>(f);
+      VIE_REQUIRE(nv >= 4 && nv < (int64_t(1) << 31), VIE_EINVAL, "vie_load: bad vertex count");
+      std::vector<double> xyz(3 * nv);
+      rd(f, xyz.data(), sizeof(double) * xyz.size());
+      const int64_t nt = rdv<int64_t>(f);
+      VIE_REQUIRE(nt >= 1 && nt < (int64_t(1) << 29), VIE_EINVAL, "vie_load: bad tet count");
+      std::vector<int32_t> tet(4 * nt);
+      std::vector<double> eps(2 * nt);
+      rd(f, tet.data(), sizeof(int32_t) * tet.size());
+      rd(f, eps.data(), sizeof(double) * eps.size());
+      const vie_mesh mm{nv, xyz.data(), nt, tet.data(), eps.data()};
+      build_mesh_general(mm, h->mesh);
+      geometry_upload(h->mesh, k0, h->geo, s);
+    } else {
+      std::vector<int32_t> ijk(3 * nvox);
+      std::vector<double> eps(2 * nvox);
+      rd(f, ijk.data(), sizeof(int32_t) * ijk.size());
+      rd(f, eps.data(), sizeof(double) * eps.size());
+      const vie_voxels body{nvox, ijk.data(), eps.data(), hh};
+      build_mesh(body, h->mesh);
+      geometry_upload(h->mesh, k0, h->geo, s);
+      geometry_table(h->geo, s);
+    }
     const int64_t N = h->mesh.nf;
-    std::vector<double> pts(3 * N);
-    for (int64_t fc = 0; fc < N; ++fc)
-      for (int d = 0; d < 3; ++d) {
-        double a = double(h->mesh.vlat[3 * h->mesh.faces[3 * fc] + d]) * h->mesh.h;
-        double b = double(h->mesh.vlat[3 * h->mesh.faces[3 * fc + 1] + d]) * h->mesh.h;
-        double c = double(h->mesh.vlat[3 * h->mesh.faces[3 * fc + 2] + d]) * h->mesh.h;
-        pts[3 * fc + d] = ((a + b) + c) / 3.0;
-      }
+    const std::vector<double> pts = face_centroids(h->mesh);
     build_tree(pts, h->cfg.leaf, h->tree);
     h->perm.alloc(sizeof(int32_t) * N);
     VIE_CUDA(cudaMemcpyAsync(h->perm.p, h->tree.perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
@@ -205,6 +226,7 @@ extern "C" vie_status vie_load(const char* path, void* stream, vie_op** out) {
     for (Program* pp : {&h->z, &h->zinv}) {  // the wait flag of the bounded-wait kernels
       pp->err.alloc(sizeof(int));
       VIE_CUDA(cudaMemsetAsync(pp->err.p, 0, sizeof(int), s));
+      pp->tc_tf32 = h->cfg.prec == VIE_P_TC_TF32;
     }
     VIE_CUDA(cudaStreamSynchronize(s));
     *out = h;

@@ -6,14 +6,18 @@
 // next step.  A step advances every admitted request by one Arnoldi iteration
 // of right-preconditioned GMRES (the same method as vie_solve): the current
 // basis vectors of all active columns of one operator are packed into one
-// multi-column block and pass through Zinv and Z together (tensor-core stages
-// when the block has 16 or more columns), then every column is orthogonalized
-// (classical Gram-Schmidt twice, FP64) by batched kernels over all requests.
+// multi-column block, and the blocks of all operators pass through Zinv and Z
+// in one grouped sequence of launches (one per stage depth, a work list over
+// operators, blocks and tiles; tensor-core items for blocks of 16 or more
+// columns), replayed from a CUDA graph while the mix of operators and column
+// counts stays the same; then every column is orthogonalized (classical
+// Gram-Schmidt twice, FP64) by batched kernels over all requests.
 // Restart cycles end with x += M V y and an FP64 refinement residual
 // r = b - Z x, which also decides convergence; the Krylov state stays on the
 // device for the whole life of the request.
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <complex>
 #include <deque>
 #include <map>
@@ -36,10 +40,11 @@ struct ColDesc {      // one right-hand side column of one request
   int32_t pad;
 };
 
-struct PackDesc {     // column `col` of a packed c64 block <-> one c128 vector
-  double2* v;
+struct OpPack {       // the packed columns of one operator in a step
+  const int32_t* perm; // cluster-tree permutation of the operator
+  float2* t;           // tree-ordered c64 block, n x ncol, columns fastest
   int64_t n;
-  int64_t col;
+  int32_t ncol, col0;  // its columns, and the first of them in the column-pointer table
 };
 
 __global__ void k_dots(const ColDesc* cols, int ncols, int kmax) {
@@ -103,17 +108,27 @@ __global__ void k_store(const ColDesc* cols, int ncols, const double* scale, int
   }
 }
 
-__global__ void k_pack(const PackDesc* p, int np, float2* out, int64_t ld) {
-  const PackDesc d = p[blockIdx.y];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < d.n; t += (int64_t)gridDim.x * blockDim.x)
-    out[d.col * ld + t] = make_float2((float)d.v[t].x, (float)d.v[t].y);
+// t[i * ncol + j] = (c64) V_j[perm[i]]: the columns of each operator into its tree-ordered block
+__global__ void k_pack_gather(const OpPack* ops, const double2* const* cols) {
+  const OpPack d = ops[blockIdx.y];
+  const int64_t tot = d.n * d.ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d.ncol;
+    const int j = int(e % d.ncol);
+    const double2 v = cols[d.col0 + j][d.perm[i]];
+    d.t[e] = make_float2((float)v.x, (float)v.y);
+  }
 }
 
-__global__ void k_unpack(const PackDesc* p, int np, const float2* in, int64_t ld) {
-  const PackDesc d = p[blockIdx.y];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < d.n; t += (int64_t)gridDim.x * blockDim.x) {
-    float2 v = in[d.col * ld + t];
-    d.v[t] = make_double2(v.x, v.y);
+// W_j[perm[i]] = (c128) t[i * ncol + j]: each operator's result block back to its columns
+__global__ void k_scatter_unpack(const OpPack* ops, double2* const* cols) {
+  const OpPack d = ops[blockIdx.y];
+  const int64_t tot = d.n * d.ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d.ncol;
+    const int j = int(e % d.ncol);
+    const float2 v = d.t[e];
+    cols[d.col0 + j][d.perm[i]] = make_double2(v.x, v.y);
   }
 }
 
@@ -196,16 +211,22 @@ struct Server {
   cudaStream_t s = nullptr;
   DevBuf cols, packs, nrm, scale, blk_a, blk_b, hall;
   int64_t steps = 0;
-  // one stream, event pair and packed blocks per operator: the applies of different
-  // operators in one step run concurrently (fork from s, join back into s)
-  std::vector<cudaStream_t> op_s;
-  std::vector<cudaEvent_t> op_done;
-  cudaEvent_t fork = nullptr;
-  std::vector<DevBuf> op_a, op_b;
+  // the grouped matvec of a step: per operator a tree-ordered block pair and a
+  // coefficient block (grown as needed), a descriptor table, and CUDA graphs of the
+  // launch sequence keyed by the operators, their column counts and the buffers
+  std::vector<DevBuf> op_a, op_b, op_c;
+  DevBuf table;
+  struct StepGraph {
+    std::vector<int64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+  };
+  std::vector<StepGraph> graphs;
+  uint64_t graph_clock = 0;
+  cudaStream_t capture = nullptr;
   ~Server() {
-    for (auto st : op_s) if (st) cudaStreamDestroy(st);
-    for (auto ev : op_done) if (ev) cudaEventDestroy(ev);
-    if (fork) cudaEventDestroy(fork);
+    for (auto& g : graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (capture) cudaStreamDestroy(capture);
   }
 };
 
@@ -343,61 +364,108 @@ static void arnoldi_step(Server& S) {
   if (reqs.empty()) return;
   std::map<int, std::vector<Req*>> by_op;
   for (Req* q : reqs) by_op[q->op].push_back(q);
-  if (S.op_s.empty()) {
-    S.op_s.assign(S.ops.size(), nullptr);
-    S.op_done.assign(S.ops.size(), nullptr);
-    S.op_a.resize(S.ops.size());
-    S.op_b.resize(S.ops.size());
-    for (size_t i = 0; i < S.ops.size(); ++i) {
-      VIE_CUDA(cudaStreamCreateWithFlags(&S.op_s[i], cudaStreamNonBlocking));
-      VIE_CUDA(cudaEventCreateWithFlags(&S.op_done[i], cudaEventDisableTiming));
-    }
-    VIE_CUDA(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming));
-  }
-  // fork: every operator's pack, Zinv and Z applies and unpack on its own stream, so the
-  // operators of the mix overlap on the device; join back into s before the orthogonalization
-  VIE_CUDA(cudaEventRecord(S.fork, S.s));
-  std::vector<DevBuf> descs;  // pack descriptors of every operator, alive until the step synchronizes
-  descs.reserve(2 * by_op.size());
+  // Z (Zinv v) for the current basis vector of every column: the columns of each operator
+  // packed into one tree-ordered block, all operators' blocks in one grouped launch sequence
+  if (S.op_a.empty()) { S.op_a.resize(S.ops.size()); S.op_b.resize(S.ops.size()); S.op_c.resize(S.ops.size()); }
+  const int nop = (int)by_op.size();
+  std::vector<OpPack> pin, pout;
+  std::vector<const double2*> cin;
+  std::vector<double2*> cout;
+  std::vector<GroupJob> jinv, jz;
+  std::vector<int64_t> key;
+  int64_t nmax_blk = 1;
   for (auto& kv : by_op) {
     const int oi = kv.first;
     vie_op* h = S.ops[oi];
-    cudaStream_t os = S.op_s[oi];
-    VIE_CUDA(cudaStreamWaitEvent(os, S.fork, 0));
     const int64_t n = h->mesh.nf;
-    std::vector<PackDesc> pin, pout;
-    int64_t ncol = 0;
+    int ncol = 0;
     for (Req* q : kv.second)
       for (int c = 0; c < q->nrhs; ++c) {
-        pin.push_back(PackDesc{q->V.as<double2>() + ((int64_t)c * (S.m + 1) + q->k) * n, n, ncol});
-        pout.push_back(PackDesc{q->w.as<double2>() + (int64_t)c * n, n, ncol});
+        cin.push_back(q->V.as<double2>() + ((int64_t)c * (S.m + 1) + q->k) * n);
+        cout.push_back(q->w.as<double2>() + (int64_t)c * n);
         ++ncol;
       }
-    const size_t need = sizeof(float2) * (size_t)n * ncol;
-    if (S.op_a[oi].bytes < need) { S.op_a[oi].alloc(need); S.op_b[oi].alloc(need); }
-    descs.emplace_back();
-    DevBuf& dpi = descs.back();
-    descs.emplace_back();
-    DevBuf& dpo = descs.back();
-    dpi.alloc(sizeof(PackDesc) * pin.size());
-    dpo.alloc(sizeof(PackDesc) * pout.size());
-    VIE_CUDA(cudaMemcpyAsync(dpi.p, pin.data(), sizeof(PackDesc) * pin.size(), cudaMemcpyHostToDevice, os));
-    VIE_CUDA(cudaMemcpyAsync(dpo.p, pout.data(), sizeof(PackDesc) * pout.size(), cudaMemcpyHostToDevice, os));
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (n + 255) / 256)), (unsigned)ncol);
-    k_pack<<<grid, 256, 0, os>>>(dpi.as<PackDesc>(), (int)ncol, S.op_a[oi].as<float2>(), n);
-    float2 *u = S.op_a[oi].as<float2>(), *v = S.op_b[oi].as<float2>();
-    if (h->has_zinv) {
-      op_apply(h, VIE_OP_ZINV, u, v, ncol, VIE_C64, os);
-      op_apply(h, VIE_OP_Z, v, u, ncol, VIE_C64, os);
-    } else {
-      op_apply(h, VIE_OP_Z, u, v, ncol, VIE_C64, os);
-      std::swap(u, v);
+    Program& pz = h->z;
+    Program* pinv = h->has_zinv ? &h->zinv : nullptr;
+    for (Program* p : {&pz, pinv}) {
+      if (!p) continue;
+      VIE_REQUIRE(p->factor_dtype == VIE_C64, VIE_EINVAL, "serving needs c64 factors");
+      if (ncol >= p->tc_min_rhs) program_prepare_tc(*p, S.s);
     }
-    k_unpack<<<grid, 256, 0, os>>>(dpo.as<PackDesc>(), (int)ncol, u, n);
-    VIE_CUDA(cudaGetLastError());
-    VIE_CUDA(cudaEventRecord(S.op_done[oi], os));
-    VIE_CUDA(cudaStreamWaitEvent(S.s, S.op_done[oi], 0));
+    const size_t vec = sizeof(float2) * (size_t)n * ncol;
+    const size_t cbytes = sizeof(float2) * (size_t)std::max(pz.ncoef, pinv ? pinv->ncoef : 0) * ncol;
+    if (S.op_a[oi].bytes < vec) { S.op_a[oi].alloc(vec); S.op_b[oi].alloc(vec); }
+    if (S.op_c[oi].bytes < std::max<size_t>(cbytes, 8)) S.op_c[oi].alloc(std::max<size_t>(cbytes, 8));
+    float2 *A = S.op_a[oi].as<float2>(), *B = S.op_b[oi].as<float2>(), *C = S.op_c[oi].as<float2>();
+    const int col0 = (int)cin.size() - ncol;
+    // Zinv: A -> B, then Z: B -> A; without an inverse Z: A -> B
+    pin.push_back(OpPack{h->perm.as<int32_t>(), A, n, ncol, col0});
+    pout.push_back(OpPack{h->perm.as<int32_t>(), pinv ? A : B, n, ncol, col0});
+    if (pinv) {
+      jinv.push_back(GroupJob{pinv, ncol, A, B, C});
+      jz.push_back(GroupJob{&pz, ncol, B, A, C});
+    } else {
+      jz.push_back(GroupJob{&pz, ncol, A, B, C});
+    }
+    nmax_blk = std::max<int64_t>(nmax_blk, n * ncol);
+    for (int64_t v : {(int64_t)oi, (int64_t)ncol, (int64_t)(uintptr_t)A, (int64_t)(uintptr_t)B, (int64_t)(uintptr_t)C})
+      key.push_back(v);
   }
+  // descriptor table: [pack-in x nop][pack-out x nop][column pointers in][column pointers out]
+  const int ncol_all = (int)cin.size();
+  const size_t tab_bytes = sizeof(OpPack) * 2 * nop + sizeof(void*) * 2 * (size_t)ncol_all;
+  if (S.table.bytes < tab_bytes) S.table.alloc(tab_bytes * 2);
+  std::vector<uint8_t> tab(tab_bytes);
+  std::memcpy(tab.data(), pin.data(), sizeof(OpPack) * nop);
+  std::memcpy(tab.data() + sizeof(OpPack) * nop, pout.data(), sizeof(OpPack) * nop);
+  std::memcpy(tab.data() + sizeof(OpPack) * 2 * nop, cin.data(), sizeof(void*) * ncol_all);
+  std::memcpy(tab.data() + sizeof(OpPack) * 2 * nop + sizeof(void*) * ncol_all, cout.data(), sizeof(void*) * ncol_all);
+  VIE_CUDA(cudaMemcpyAsync(S.table.p, tab.data(), tab_bytes, cudaMemcpyHostToDevice, S.s));
+  key.push_back((int64_t)(uintptr_t)S.table.p);
+  key.push_back(ncol_all);
+  Server::StepGraph* hit = nullptr;
+  for (auto& g : S.graphs)
+    if (g.exec && g.key == key) hit = &g;
+  if (!hit) {
+    if (S.graphs.size() < kGraphCache) {
+      S.graphs.emplace_back();
+      hit = &S.graphs.back();
+    } else {
+      hit = &S.graphs[0];
+      for (auto& g : S.graphs)
+        if (g.used < hit->used) hit = &g;
+      if (hit->exec) { cudaGraphExecDestroy(hit->exec); hit->exec = nullptr; }
+    }
+    if (!S.capture) VIE_CUDA(cudaStreamCreateWithFlags(&S.capture, cudaStreamNonBlocking));
+    uint8_t* T = S.table.as<uint8_t>();
+    const OpPack* d_in = reinterpret_cast<const OpPack*>(T);
+    const OpPack* d_out = reinterpret_cast<const OpPack*>(T + sizeof(OpPack) * nop);
+    const double2* const* d_cin = reinterpret_cast<const double2* const*>(T + sizeof(OpPack) * 2 * nop);
+    double2* const* d_cout =
+        reinterpret_cast<double2* const*>(T + sizeof(OpPack) * 2 * nop + sizeof(void*) * ncol_all);
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(256, (nmax_blk + 255) / 256)), (unsigned)nop);
+    cudaGraph_t g = nullptr;
+    VIE_CUDA(cudaStreamBeginCapture(S.capture, cudaStreamCaptureModeThreadLocal));
+    try {
+      k_pack_gather<<<grid, 256, 0, S.capture>>>(d_in, d_cin);
+      VIE_CUDA(cudaGetLastError());
+      group_run_stages(jinv, S.capture);
+      group_run_stages(jz, S.capture);
+      k_scatter_unpack<<<grid, 256, 0, S.capture>>>(d_out, d_cout);
+      VIE_CUDA(cudaGetLastError());
+    } catch (...) {
+      cudaStreamEndCapture(S.capture, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    VIE_CUDA(cudaStreamEndCapture(S.capture, &g));
+    cudaError_t ie = cudaGraphInstantiate(&hit->exec, g, 0);
+    cudaGraphDestroy(g);
+    VIE_CUDA(ie);
+    hit->key = key;
+  }
+  hit->used = ++S.graph_clock;
+  VIE_CUDA(cudaGraphLaunch(hit->exec, S.s));
 
   // batched CGS2 over every column of every iterating request
   std::vector<ColDesc> cds;
@@ -514,7 +582,10 @@ vie_status vie_server_create(vie_op* const* ops, int32_t nops, int32_t restart, 
   return guarded_s([&] {
     VIE_REQUIRE(ops && nops >= 1 && out && restart >= 1 && max_iter >= 1 && mem_budget > 0, VIE_EINVAL,
                 "bad server arguments");
-    for (int i = 0; i < nops; ++i) VIE_REQUIRE(ops[i] != nullptr, VIE_EINVAL, "null operator");
+    for (int i = 0; i < nops; ++i) {
+      VIE_REQUIRE(ops[i] != nullptr, VIE_EINVAL, "null operator");
+      VIE_REQUIRE(ops[i]->z.factor_dtype == VIE_C64, VIE_EINVAL, "serving needs operators with c64 factors");
+    }
     auto* sv = new vie_server();
     sv->S.ops.assign(ops, ops + nops);
     sv->S.m = restart;

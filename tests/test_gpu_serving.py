@@ -40,7 +40,7 @@ def _run(srv, ids, n_of, nrhs_of, max_steps=2000):
 
 def test_same_result_alone_and_in_the_mix(ops, lossy_sphere):
     """Requests on three operators (a lossy sphere, a Drude shell, an eps_r = 10 sphere) whose
-    applies overlap on the device within each step; the request on the first operator gives
+    applies run in one grouped launch sequence per step; the request on the first operator gives
     the same solution alone and in the mix, and both solutions are within 1e-3 of the oracle's
     dense LU (residual rtol 2e-4 buys the 1e-3 solution accuracy at which the serving speed-up
     is stated)."""

@@ -1,9 +1,9 @@
-"""Config 1 as the plain FP64 method: homogeneous lossless sphere r = 0.3 lambda0, eps_r = 4,
+"""The plain FP64 method on the homogeneous lossless sphere r = 0.3 lambda0, eps_r = 4,
 pitch lambda_d/10 (N = 11,616), complex FP64 factors (VIE_P_FP64) at chi_con 1e-4, Zinv at
 chi_fact 1e-1, GMRES to rtol 1e-6, against the oracle's dense LU of the same discretization
 (Eq. 5, assembled in parallel worker processes) and the Mie series.
 
-The RCS rule of the benchmark spec (within 0.5 dB of Mie) is checked against the exact discrete
+The RCS acceptance rule (within 0.5 dB of Mie) is checked against the exact discrete
 solution instead of Mie: the dense-LU solution of this voxel mesh itself deviates from the
 Mie series of the equal-volume sphere by up to 1.4 dB (E plane) and 1.7 dB (H plane) at
 angles within 20 dB of the peak (staircase surface; reading Q21)."""
@@ -26,7 +26,7 @@ from oracle.mie import rcs_sphere  # noqa: E402
 from oracle_pool import dense_z  # noqa: E402
 
 
-def test_config1_fp64_solve_matches_dense_lu_and_rcs():
+def test_sphere_fp64_solve_matches_dense_lu_and_rcs():
     body = W.sphere_small_fp64()
     Z = dense_z(body, W.K0)
     mesh = build_mesh(body)
@@ -50,7 +50,7 @@ def test_config1_fp64_solve_matches_dense_lu_and_rcs():
         m = rcs_sphere(req, 4.0, np.radians(th), np.radians(ph))
         sel = o >= o.max() * 1e-2  # within 20 dB of the peak (reading Q21)
         out[ph] = (np.abs(10 * np.log10(g[sel] / o[sel])).max(), np.abs(10 * np.log10(o[sel] / m[sel])).max())
-    print("config 1 FP64: GMRES iterations", it[0], "solution vs dense LU", err,
+    print("sphere r=0.3 eps 4 N=11,616 FP64: GMRES iterations", it[0], "solution vs dense LU", err,
           "max |dB| GPU vs dense LU / dense LU vs Mie (E, H):", out)
     assert err < 1e-3
     for ph in out:

@@ -1,0 +1,129 @@
+"""General tetrahedral meshes on the GPU (vie_build_mesh) against the oracle's general path:
+off-lattice five-tet meshes with jittered vertices (a lossy sphere; a Drude shell with charge
+jumps and half-SWG faces) and a Kuhn mesh handed over as a general mesh.  Mesh and tree bit
+for bit, FP64 entries and right-hand sides to rounding, the compressed apply within the
+compression bound, the preconditioned solve against the oracle's dense LU, a checkpoint round
+trip."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2111_01730_gb300 as pkg  # noqa: E402
+from oracle.dense import rcs, solve_dense  # noqa: E402
+from oracle.entries import Elements, rhs_planewave, zblock  # noqa: E402
+from oracle.hodbf import cluster_tree, face_centroids  # noqa: E402
+from oracle.mesh import build_mesh, build_mesh_general  # noqa: E402
+
+
+class _Kuhn:
+    def __init__(self, body):
+        m = build_mesh(body)
+        self.verts, self.tets, self.eps, self.body = m["verts"], m["tets"], m["eps"], body
+
+
+MESHES = {
+    "sphere_tet5": lambda: W.tet_body(W.sphere(0.2, 4.0 - 1.0j, 1.0 / 16), jitter=0.08, seed=1),
+    "shell_tet5": lambda: W.tet_body(W.shell(0.25, 0.15, W.drude_eps(), 1.0 / 20), jitter=0.1, seed=2),
+    "kuhn_general": lambda: _Kuhn(W.sphere(0.2, 4.0 - 1.0j, 1.0 / 16)),
+}
+
+
+@pytest.fixture(scope="module", params=list(MESHES))
+def case(request):
+    m = MESHES[request.param]()
+    mesh = build_mesh_general(m.verts, m.tets, m.eps)
+    E = Elements(mesh, W.K0)
+    n = len(mesh["faces"])
+    Z = zblock(E, np.arange(n), np.arange(n))
+    return dict(name=request.param, m=m, mesh=mesh, E=E, Z=Z, n=n)
+
+
+def test_mesh_and_tree_bit_exact(case):
+    op = pkg.Operator(case["m"], W.K0, tol_con=1e-4, leaf=64)
+    f, tp, tm = op.faces()
+    mesh = case["mesh"]
+    assert op.n == case["n"]
+    assert np.array_equal(f, mesh["faces"]) and np.array_equal(tp, mesh["face_tp"])
+    assert np.array_equal(tm, mesh["face_tm"])
+    perm, LH, _ = cluster_tree(face_centroids(mesh), 64)
+    assert op.stats.levels == LH and np.array_equal(op.tree_perm(), perm)
+
+
+def test_entries_and_rhs_fp64(case):
+    op = pkg.Operator(case["m"], W.K0, tol_con=1e-4, leaf=64)
+    n = case["n"]
+    r, c = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    rows = torch.from_numpy(r.ravel().astype(np.int32)).cuda()
+    cols = torch.from_numpy(c.ravel().astype(np.int32)).cuda()
+    z = op.entries(rows, cols).cpu().numpy().reshape(n, n)
+    Z = case["Z"]
+    err = np.abs(z - Z).max() / np.abs(Z).max()
+    print(case["name"], "N", n, "entries vs oracle", err)
+    assert err < 1e-10, err
+    k, p = W.planewave_grid(2, 3)
+    V = op.rhs_planewave(k, p).cpu().numpy()
+    Vo = rhs_planewave(case["E"], k, p)
+    assert np.abs(V - Vo).max() < 1e-12 * np.abs(Vo).max()
+
+
+@pytest.mark.parametrize("tol,bound", [(1e-4, 5e-4), (1e-3, 5e-3)])
+def test_apply_vs_dense(case, tol, bound):
+    op = pkg.Operator(case["m"], W.K0, tol_con=tol, leaf=64)
+    for nrhs in (1, 16):
+        X = W.random_block(case["n"], nrhs, seed=nrhs)
+        ref = case["Z"] @ X
+        Y = op.apply(torch.from_numpy(X).to(torch.complex64).cuda()).cpu().numpy()
+        err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+        assert err < bound, (nrhs, err)
+
+
+def test_kuhn_mesh_as_general_matches_voxel_build(case):
+    """The general evaluator on a Kuhn mesh gives the lattice evaluator's entries."""
+    if case["name"] != "kuhn_general":
+        pytest.skip("Kuhn mesh only")
+    og = pkg.Operator(case["m"], W.K0, tol_con=1e-4, leaf=64)
+    ov = pkg.Operator(case["m"].body, W.K0, tol_con=1e-4, leaf=64)
+    n = case["n"]
+    g = torch.Generator().manual_seed(3)
+    rows = torch.randint(0, n, (20000,), generator=g, dtype=torch.int32).cuda()
+    cols = torch.randint(0, n, (20000,), generator=g, dtype=torch.int32).cuda()
+    a, b = og.entries(rows, cols), ov.entries(rows, cols)
+    assert (torch.abs(a - b).max() / torch.abs(b).max()).item() < 1e-12
+
+
+def test_solve_vs_dense_lu_and_checkpoint(case, tmp_path):
+    """Zinv-preconditioned GMRES (FP64 refinement) to 1e-6 against the dense LU solution of the
+    same discretization; backscatter RCS within 0.05 dB of the LU one; a saved and reloaded
+    operator applies bit-identically.  chi_fact as in the paper: 1e-1 for the dielectric,
+    1e-3 for the negative-permittivity shell (Sec. IV-A)."""
+    if case["name"] == "kuhn_general":
+        pytest.skip("covered by the voxel path")
+    fact = 1e-3 if np.real(case["m"].eps).min() < 0 else 1e-1
+    op = pkg.Operator(case["m"], W.K0, tol_con=1e-5, tol_fact=fact, leaf=64)
+    k, p = W.planewave_x_along_z()
+    V = op.rhs_planewave(k, p)
+    I, it, rel, st = op.solve(V, rtol=1e-6)
+    assert st == pkg.VIE_OK
+    Vo = rhs_planewave(case["E"], k, p)
+    Io = solve_dense(case["Z"], Vo)
+    Ig = I.cpu().numpy()
+    err = np.linalg.norm(Ig - Io) / np.linalg.norm(Io)
+    dirs = np.array([[0.0, 0.0, -1.0], [1.0, 0.0, 0.0], [0.0, 0.6, 0.8]])
+    sg = op.farfield_rcs(I, dirs)[:, 0]
+    so = rcs(case["E"], Io, dirs)[:, 0]
+    ddb = np.abs(10 * np.log10(sg / so)).max()
+    print(case["name"], "GMRES iterations", it[0], "solution vs LU", err, "max |dRCS| dB", ddb)
+    assert err < 1e-3 and ddb < 0.05
+    path = str(tmp_path / "tet.vie")
+    op.save(path)
+    op2 = pkg.Operator.load(path)
+    X = torch.from_numpy(W.random_block(case["n"], 3, seed=5)).to(torch.complex64).cuda()
+    assert torch.equal(op.apply(X), op2.apply(X))
+    assert torch.equal(op.apply(X, op=pkg.VIE_OP_ZINV), op2.apply(X, op=pkg.VIE_OP_ZINV))

@@ -1,8 +1,8 @@
 """Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
 
 This module holds input *data* only: the scatterer descriptions (a list of
-voxels with their relative permittivity), seeded random block vectors and
-plane-wave sets.  It contains none of the method's arithmetic (no mesh
+voxels with their relative permittivity, or a general tetrahedral mesh given by
+its vertices and tets), seeded random block vectors and plane-wave sets.  It contains none of the method's arithmetic (no mesh
 splitting, no basis functions, no matrix entries, no compression): the
 oracle and the CUDA library each build those from these inputs on their own.
 
@@ -93,6 +93,49 @@ def cube_grf(side: float, h: float, corr: float = 0.5, seed: int = 20211101,
     u = ndtr(z).ravel()
     eps = (eps_lo + eps_span * u).astype(np.complex128)
     return VoxelBody(name, h, ijk, eps)
+
+
+@dataclasses.dataclass(frozen=True)
+class TetMesh:
+    """A general tetrahedral mesh given as data: vertex coordinates, 4 vertex ids per tet
+    (any orientation) and eps_r per tet."""
+
+    name: str
+    verts: np.ndarray  # (nv, 3) float64
+    tets: np.ndarray   # (nt, 4) int32
+    eps: np.ndarray    # (nt,) complex128
+
+
+# the five tetrahedra of a unit cube (corner bits x, y, z), by cube parity: for even cubes
+# the tet of the four even corners plus one tet per odd corner, for odd cubes the mirror;
+# neighbouring cubes have opposite parity and share their face diagonals
+_CUBE5 = {
+    0: [[0b000, 0b110, 0b101, 0b011], [0b100, 0b000, 0b110, 0b101], [0b010, 0b000, 0b110, 0b011],
+        [0b001, 0b000, 0b101, 0b011], [0b111, 0b110, 0b101, 0b011]],
+    1: [[0b100, 0b010, 0b001, 0b111], [0b000, 0b100, 0b010, 0b001], [0b110, 0b100, 0b010, 0b111],
+        [0b101, 0b100, 0b001, 0b111], [0b011, 0b010, 0b001, 0b111]],
+}
+
+
+def tet_body(body: VoxelBody, jitter: float = 0.08, seed: int = 5, name: str | None = None) -> TetMesh:
+    """The voxels of ``body`` cut into five tetrahedra each (alternating cube parity, a
+    conforming mesh unlike the Kuhn split), with every vertex moved by a seeded uniform
+    offset of up to ``jitter`` * h per coordinate, so the elements are off any lattice.
+    Vertices are the distinct lattice corners in lexicographic order; tets are
+    voxel-major, five per voxel; eps_r of a tet is that of its voxel."""
+    ijk = np.asarray(body.ijk, dtype=np.int64)
+    corners = []
+    for v in ijk:
+        par = int(v.sum()) % 2
+        for t in _CUBE5[par]:
+            corners.append([[v[0] + (c >> 2 & 1), v[1] + (c >> 1 & 1), v[2] + (c & 1)] for c in t])
+    lat = np.asarray(corners, dtype=np.int64)  # (nt, 4, 3)
+    uniq, inv = np.unique(lat.reshape(-1, 3), axis=0, return_inverse=True)
+    rng = np.random.default_rng(seed)
+    verts = (uniq.astype(np.float64) + rng.uniform(-jitter, jitter, size=uniq.shape)) * body.h
+    tets = inv.reshape(-1, 4).astype(np.int32)
+    eps = np.repeat(np.asarray(body.eps, dtype=np.complex128), 5)
+    return TetMesh(name or body.name + "_tet5", verts, tets, eps)
 
 
 # --------------------------------------------------------------------------------------
