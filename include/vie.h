@@ -253,8 +253,9 @@ vie_status vie_autotune_rhs(vie_op* op, int32_t which, int32_t* tc_min_rhs, void
  * prec = VIE_P_C32 (SIMT only), VIE_P_TC_BF16X3 or VIE_P_TC_TF32 (tensor cores
  * from 16 columns).  Waits for the device, drops the packed tensor-core tiles and
  * captured graphs of Z and Zinv (repacked on the next multi-RHS apply) and sets
- * vie_config.prec.  VIE_EINVAL: null op, another prec value, complex FP64
- * factors. */
+ * vie_config.prec.  Not while a server (vie_server_create) holds the operator:
+ * its captured steps keep the old tiles.  VIE_EINVAL: null op, another prec
+ * value, complex FP64 factors. */
 vie_status vie_set_prec(vie_op* op, int32_t prec);
 
 /* Block shapes of one stage of an apply program (introspection for profiling):
