@@ -30,7 +30,7 @@ class _Kuhn:
 
 MESHES = {
     "sphere_tet5": lambda: W.tet_body(W.sphere(0.2, 4.0 - 1.0j, 1.0 / 16), jitter=0.08, seed=1),
-    "shell_tet5": lambda: W.tet_body(W.shell(0.25, 0.15, W.drude_eps(), 1.0 / 20), jitter=0.1, seed=2),
+    "shell_tet5": lambda: W.tet_body(W.shell(0.22, 0.12, W.drude_eps(), 1.0 / 20), jitter=0.1, seed=2),
     "kuhn_general": lambda: _Kuhn(W.sphere(0.2, 4.0 - 1.0j, 1.0 / 16)),
 }
 

@@ -1,7 +1,10 @@
 """Full-size parity: the benchmark workload (sphere r = 2, N = 410,208) in the benchmark's launch
 configuration, checked on 64 sampled output rows that the oracle computes (Eq. 5 rows), and its
 preconditioned solve (the complete inverse, upper levels from products only) checked by sampled
-residual rows and against the Mie series."""
+residual rows and against the Mie series.  Building the complete inverse of this operator takes
+about 20 minutes, so the solve runs only with VIE_FULLSIZE_SOLVE=1 in the environment:
+    VIE_FULLSIZE_SOLVE=1 python -m pytest tests/test_gpu_z1_fullsize_sphere.py -m gpu -s"""
+import os
 import time
 
 import numpy as np
@@ -23,10 +26,15 @@ from oracle.mie import rcs_sphere  # noqa: E402
 from oracle_pool import z_rows  # noqa: E402
 
 
+SOLVE = os.environ.get("VIE_FULLSIZE_SOLVE") == "1"
+
+
 @pytest.fixture(scope="module")
 def full():
+    """The benchmark operator; with the complete inverse (chi_fact 1e-2) when the solve runs."""
     body = W.sphere_large_c32()
-    op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=1e-2, leaf=64, factor_dtype="c64", seed=1)
+    op = pkg.Operator(body, W.K0, tol_con=1e-4, tol_fact=1e-2 if SOLVE else 0.0, leaf=64, factor_dtype="c64",
+                      seed=1)
     op.autotune()
     mesh = build_mesh(body)
     yield body, op, mesh
@@ -57,6 +65,7 @@ def test_full_size_apply_is_finite_and_linear(full):
     assert (torch.linalg.norm(c - (a + 2.0 * b)) / torch.linalg.norm(c)).item() < 1e-5
 
 
+@pytest.mark.skipif(not SOLVE, reason="complete inverse of N = 410,208 (about 20 min): set VIE_FULLSIZE_SOLVE=1")
 def test_full_size_solve_residual_rows_and_rcs_vs_mie(full):
     """The complete inverse (levels 0-2, nodes of 103k-410k unknowns, from products only;
     chi_fact 1e-2, reading Q20) as preconditioner on the 410,208-unknown sphere: TFQMR (Eq. 6)
