@@ -224,7 +224,7 @@ def run_reference(args):
 def serving_operators():
     """Resident scatterers of the serving workload: the kinds of the eight-operator mix (spheres
     of eps_r 2, 4, 10 and 40, a negative-permittivity shell, a lossy sphere) at reduced sizes
-    (N = 6.9k-27.7k; the full mix holds 1.18 M unknowns), pitch lambda_d/10, capped at
+    (N = 7.1k-27.7k; the full mix holds 1.18 M unknowns), pitch lambda_d/10, capped at
     lambda0/20 for eps_r = 40 as in the mix."""
     r2 = 1.0 / (10 * 2 ** 0.5)
     r10 = 1.0 / (10 * 10 ** 0.5)
