@@ -110,6 +110,7 @@ static void check_config(const vie_config* cfg, double k0) {
 
 // everything after the mesh: geometry, cluster tree, Z (Sec. III-A), Zinv (Sec. III-B)
 static void build_operator(vie_op* h, double k0, const vie_config* cfg, cudaStream_t s, double t0) {
+  Trace tr("vie:build");
   h->cfg = *cfg;
   if (h->cfg.oversample <= 0) h->cfg.oversample = 10;
   if (cfg->prec == VIE_P_FP64) h->cfg.factor_dtype = VIE_C128;
@@ -125,7 +126,10 @@ static void build_operator(vie_op* h, double k0, const vie_config* cfg, cudaStre
   VIE_CUDA(cudaMemcpyAsync(h->tet_faces.p, h->mesh.tet_faces.data(), sizeof(int32_t) * 4 * h->mesh.nt,
                            cudaMemcpyHostToDevice, s));
   BuildResult br;
-  build_hodbf(h, s, br);
+  {
+    Trace tz("vie:build/Z");
+    build_hodbf(h, s, br);
+  }
   const int never = 1 << 30;
   h->z.tc_min_rhs = h->zinv.tc_min_rhs = cfg->prec == VIE_P_C32 ? never : kTcMinRhs;
   VIE_CUDA(cudaStreamSynchronize(s));
@@ -144,6 +148,7 @@ static void build_operator(vie_op* h, double k0, const vie_config* cfg, cudaStre
   if (cfg->tol_fact > 0) {
     double t1 = now_s();
     BuildResult bi;
+    Trace ti("vie:build/Zinv");
     build_inverse(h, s, bi);
     VIE_CUDA(cudaStreamSynchronize(s));
     h->stats.entries_zinv = h->zinv.entries;
@@ -210,6 +215,7 @@ vie_status vie_apply(vie_op* h, int32_t which, const void* X, void* Y, int64_t n
     VIE_REQUIRE(nrhs >= 1 && ldx >= h->mesh.nf && ldy >= h->mesh.nf, VIE_EINVAL, "bad nrhs or leading dimension");
     VIE_REQUIRE(dtype == VIE_C64 || dtype == VIE_C128, VIE_EINVAL, "bad dtype");
     VIE_REQUIRE(which >= VIE_OP_Z && which <= VIE_OP_ZINVH, VIE_EINVAL, "bad operator kind");
+    Trace tr(which == VIE_OP_Z ? "vie:apply/Z" : which == VIE_OP_ZINV ? "vie:apply/Zinv" : "vie:apply/adjoint");
     VIE_REQUIRE(which == VIE_OP_Z || which == VIE_OP_ZH || h->has_zinv, VIE_ENOTSUP,
                 "operator has no inverse (tol_fact <= 0)");
     cudaStream_t s = (cudaStream_t)stream;

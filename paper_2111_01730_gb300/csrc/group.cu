@@ -118,6 +118,7 @@ vie_status vie_apply_group(vie_op* const* ops, const int32_t* which, const void*
                            const int64_t* nrhs, int32_t count, void* stream) {
   try {
     VIE_REQUIRE(count >= 0 && (count == 0 || (ops && which && X && Y && nrhs)), VIE_EINVAL, "null argument");
+    Trace tr("vie:apply_group");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<GroupJob> jobs;
     for (int i = 0; i < count; ++i) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -15,6 +16,15 @@ namespace vie {
 // error handling
 // ---------------------------------------------------------------------------
 void set_error(const std::string& msg);
+
+// Tracing: an NVTX range for the lifetime of the object ("vie:<phase>"), shown by
+// Nsight Systems and other NVTX tools; without a tool attached the calls do nothing.
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
 
 struct Error {
   vie_status status;

@@ -1257,6 +1257,7 @@ std::unique_ptr<ProgOp> bf_smw(Ctx& c, LinOp& A, int lam, const std::vector<int6
 void build_inverse_products(vie_op* h, int l_top, double tol, cudaStream_t s, InverseProductStats& st) {
   if (l_top < 0) return;
   VIE_REQUIRE(h->cfg.factor_dtype == VIE_C64, VIE_ENOTSUP, "the product-built inverse needs complex FP32 factors");
+  Trace tr("vie:build/Zinv/products");
   Ctx c(h, s, tol);
   const int LH = c.t.levels;
   const auto t0 = std::chrono::steady_clock::now();

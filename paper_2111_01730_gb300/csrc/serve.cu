@@ -621,6 +621,7 @@ vie_status vie_server_submit(vie_server* sv, int32_t op, const void* V_host, int
 vie_status vie_server_step(vie_server* sv, int32_t* active, int32_t* pending) {
   return guarded_s([&] {
     VIE_REQUIRE(sv, VIE_EINVAL, "null server");
+    Trace tr("vie:server_step");
     Server& S = sv->S;
     admit(S);
     for (auto& kv : S.active)

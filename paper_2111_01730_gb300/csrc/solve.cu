@@ -184,6 +184,7 @@ void op_apply(vie_op* h, int which, const void* X, void* Y, int64_t nrhs, int dt
 
 void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int restart, int max_iter,
                  int32_t* iters_out, double* relres_out, cudaStream_t s, bool& converged_all) {
+  Trace tr("vie:solve/gmres");
   const int64_t n = h->mesh.nf;
   const int m = std::max(1, restart);
   const int ldb = m + 1, ldh = m + 1;
@@ -383,6 +384,7 @@ void solve_gmres(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, doub
 // column gets zero coefficients so that its iterate stays fixed.
 void solve_tfqmr(vie_op* h, const double2* b, double2* x_out, int64_t nrhs, double rtol, int max_iter,
                  int32_t* iters_out, double* relres_out, cudaStream_t s, bool& converged_all) {
+  Trace tr("vie:solve/tfqmr");
   const int64_t n = h->mesh.nf;
   const int64_t nb = n * nrhs;
   const bool fp64 = h->cfg.factor_dtype == VIE_C128;
