@@ -307,6 +307,10 @@ def serving_line(args):
     serve(True)  # warm-up: tensor-core tiles, workspaces
     wall_s, lat_s, rel_s, it_s = serve(True)
     wall_p, lat_p, rel_p, it_p = serve(False)
+    try:
+        grouped = grouped_timing(mixed, pkg, torch)
+    except Exception as exc:  # reported, the serving numbers stand on their own
+        grouped = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     # plain FP64 GPU solver, one request and one right-hand side at a time, on a bounded sample
     for m in mixed:
         m.close()
@@ -340,8 +344,48 @@ def serving_line(args):
                         "max_relres": float(rel_p.max())},
             "plain_fp64_one_at_a_time": {"solves_per_s": round(base, 2), "sample_rhs": done_rhs,
                                          "max_relres": max(rel_b)},
-            "speedup_vs_plain_fp64": round(total_rhs / wall_s / base, 2)}
+            "speedup_vs_plain_fp64": round(total_rhs / wall_s / base, 2),
+            "grouped_apply": grouped}
     return line
+
+
+def grouped_timing(ops, pkg, torch, reps: int = 20):
+    """Z (Zinv x) of every resident operator at 1 and 8 columns: one apply per operator (each
+    replayed from its CUDA graph) against one grouped launch sequence for all of them
+    (vie_apply_group, one launch per stage depth); CUDA events, median of the repetitions,
+    and whether the grouped results equal the separate ones bit for bit."""
+    out = {}
+    stream = torch.cuda.current_stream()
+    for nrhs in (1, 8):
+        X = [torch.from_numpy(W.random_block(o.n, nrhs, seed=21 + i).astype(np.complex64)).cuda().t().contiguous().t()
+             for i, o in enumerate(ops)]
+        jobs = [(o, x, pkg.VIE_OP_ZINV) for o, x in zip(ops, X)]
+
+        def separate():
+            return [o.apply(x, op=k) for o, x, k in jobs]
+
+        def grouped():
+            return pkg.apply_group(jobs)
+
+        same = all(torch.equal(a, b) for a, b in zip(separate(), grouped()))
+        times = {}
+        for name, fn in (("separate", separate), ("grouped", grouped)):
+            for _ in range(3):
+                fn()
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            times[name] = round(float(np.median(ms)), 4)
+        out[f"nrhs_{nrhs}"] = {"separate_ms": times["separate"], "grouped_ms": times["grouped"],
+                               "speedup": round(times["separate"] / times["grouped"], 3), "bit_identical": same}
+    out["operators"] = len(ops)
+    out["op"] = "Zinv"
+    return out
 
 
 def serving_summary(args):
@@ -352,7 +396,8 @@ def serving_summary(args):
 
     sub = argparse.Namespace(requests=40, rate=100.0, baseline_requests=2, serve_ops=6)
     full = serving_line(sub)
-    keep = ("metric", "value", "unit", "saturated", "poisson", "plain_fp64_one_at_a_time", "speedup_vs_plain_fp64")
+    keep = ("metric", "value", "unit", "saturated", "poisson", "plain_fp64_one_at_a_time", "speedup_vs_plain_fp64",
+            "grouped_apply")
     out = {k: full[k] for k in keep}
     out["config"] = {k: full["config"][k] for k in ("workload", "requests", "rhs_total", "rhs_per_request", "chi_con",
                                                     "chi_fact", "restart")}
