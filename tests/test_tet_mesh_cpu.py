@@ -189,3 +189,21 @@ def test_jittered_reciprocity_and_zero_contrast():
     Z0 = zblock(Elements(vac, W.K0), np.arange(n), np.arange(n))
     assert np.allclose(Z0.imag, 0.0, atol=1e-15) and np.allclose(Z0, Z0.T, atol=1e-15)
     assert np.all(np.linalg.eigvalsh(Z0.real) > 0)  # Gram matrix of independent SWG functions
+
+
+@lib_needed
+@pytest.mark.parametrize("offset", [(0.0, 0.0, 0.0), (37.3, -12.05, 101.7)])
+def test_host_cells_bit_exact_off_origin(offset):
+    """The tier cells and their pitch come out bit for bit the same in the library and the
+    oracle also for a mesh far from the origin, where floor(centroid / pitch) is most exposed to
+    rounding (both follow the same fixed sequence of +, -, *, / and sqrt)."""
+    import paper_2111_01730_gb300 as pkg
+
+    m = W.tet_body(W.sphere(0.15, 4.0, 1.0 / 20), jitter=0.11, seed=12)
+    verts = m.verts + np.asarray(offset)
+    m2 = W.TetMesh("shifted", verts, m.tets, m.eps)
+    r = pkg.mesh_host_tets(m2, leaf=32)
+    o = build_mesh_general(verts, m.tets, m.eps)
+    assert r["cell_pitch"] == o["h"]
+    assert np.array_equal(r["cells"], o["vox_ijk"])
+    assert np.array_equal(r["faces"], o["faces"])
