@@ -417,6 +417,16 @@ vie_status vie_server_step(vie_server* srv, int32_t* active, int32_t* pending);
 vie_status vie_server_result(vie_server* srv, int64_t id, void* I_host, int32_t* iters, double* relres,
                              double* latency_s);
 
+/* Cancel request `id` between steps: a pending request is dropped, an admitted one
+ * leaves the batch and its Krylov state is freed (its memory returns to the
+ * budget), a finished one discards its result.  The other requests continue
+ * unchanged.  VIE_EINVAL: null server or unknown id. */
+vie_status vie_server_cancel(vie_server* srv, int64_t id);
+
+/* Device bytes the admitted requests' Krylov state holds against the budget (host
+ * out-parameters, either may be NULL). */
+vie_status vie_server_memory(const vie_server* srv, int64_t* used, int64_t* budget);
+
 void vie_server_destroy(vie_server* srv);
 
 void vie_destroy(vie_op* op);

@@ -28,7 +28,7 @@ EXPORTS = ["vie_build", "vie_apply", "vie_apply_noalloc", "vie_apply_profile", "
            "vie_mesh_faces", "vie_mesh_host", "vie_tree_perm", "vie_stats", "vie_check", "vie_wait_selftest", "vie_destroy", "vie_last_error",
            "vie_server_create", "vie_server_submit", "vie_server_step", "vie_server_result", "vie_server_destroy",
            "vie_save", "vie_load", "vie_shard_range", "vie_apply_shard", "vie_apply_group", "vie_build_mesh",
-           "vie_mesh_host_tets", "vie_set_prec"]
+           "vie_mesh_host_tets", "vie_set_prec", "vie_server_cancel", "vie_server_memory"]
 
 
 class VieError(RuntimeError):
@@ -120,6 +120,8 @@ def load_library(path: str = LIB_PATH):
         "vie_build_mesh": [P, D, P, P, P],
         "vie_mesh_host_tets": [P, I32, P, P, P, P, P, P, P, P],
         "vie_set_prec": [P, I32],
+        "vie_server_cancel": [P, I64],
+        "vie_server_memory": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -536,6 +538,16 @@ class Server:
             return None
         _check(st)
         return I, it, rel, lat.value
+
+    def cancel(self, rid: int):
+        """Drop request rid (pending, running or finished); its memory returns to the budget."""
+        _check(_lib.vie_server_cancel(self._h, rid))
+
+    def memory(self):
+        """(bytes held by the admitted requests' Krylov state, budget)."""
+        used, budget = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(_lib.vie_server_memory(self._h, ctypes.byref(used), ctypes.byref(budget)))
+        return used.value, budget.value
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value and _lib is not None:

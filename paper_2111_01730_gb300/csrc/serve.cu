@@ -672,6 +672,38 @@ vie_status vie_server_result(vie_server* sv, int64_t id, void* I_host, int32_t* 
   return st;
 }
 
+vie_status vie_server_cancel(vie_server* sv, int64_t id) {
+  return guarded_s([&] {
+    VIE_REQUIRE(sv, VIE_EINVAL, "null server");
+    Server& S = sv->S;
+    for (auto it = S.pending.begin(); it != S.pending.end(); ++it)
+      if ((*it)->id == id) {
+        S.pending.erase(it);
+        return;
+      }
+    auto a = S.active.find(id);
+    if (a != S.active.end()) {
+      // between steps nothing on the stream reads the request's buffers (every step ends
+      // synchronized), and the next step's descriptor table no longer lists its columns
+      VIE_CUDA(cudaStreamSynchronize(S.s));
+      S.used -= a->second->bytes;
+      S.active.erase(a);  // frees its device buffers
+      return;
+    }
+    auto d = S.done.find(id);
+    VIE_REQUIRE(d != S.done.end(), VIE_EINVAL, "unknown request id");
+    S.done.erase(d);
+  });
+}
+
+vie_status vie_server_memory(const vie_server* sv, int64_t* used, int64_t* budget) {
+  return guarded_s([&] {
+    VIE_REQUIRE(sv, VIE_EINVAL, "null server");
+    if (used) *used = (int64_t)sv->S.used;
+    if (budget) *budget = (int64_t)sv->S.budget;
+  });
+}
+
 void vie_server_destroy(vie_server* sv) { delete sv; }
 
 }  // extern "C"
