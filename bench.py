@@ -698,16 +698,25 @@ def main():
             "clocks": clk,
         }
         if args.zinv:
-            line["zinv"] = zinv_timing(op, pkg, x, y, args.steps, torch)
+            try:
+                line["zinv"] = zinv_timing(op, pkg, x, y, args.steps, torch)
+            except Exception as exc:  # an extra key: the headline line must still print
+                line["zinv"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
         if nrhs == 1 and not args.no_extras:
-            line["multi_rhs"] = multi_rhs_timing(op, pkg, torch)
+            try:
+                line["multi_rhs"] = multi_rhs_timing(op, pkg, torch)
+            except Exception as exc:  # an extra key: the headline line must still print
+                line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
         line["roofline"].update({"peak_kind": peak_kind, "stage_ms": [round(float(v), 4) for v in stage_ms],
                                  "stage_gbs": [round(8 * float(e) / (float(t) * 1e6), 1)
                                                for e, t in zip(entries, stage_ms)]})
         if nrhs == 1 and not args.no_extras and world == 1:
             op.close()
             torch.cuda.empty_cache()
-            line["preconditioned_solve"] = precond_section(pkg, torch)
+            try:
+                line["preconditioned_solve"] = precond_section(pkg, torch)
+            except Exception as exc:  # an extra key: the headline line must still print
+                line["preconditioned_solve"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
             torch.cuda.empty_cache()
             try:
                 line["serving"] = serving_summary(args)
