@@ -49,9 +49,10 @@ void shard_forget(const vie_op* h) {
 }
 
 static void shard_range(const vie_op* h, int rank, int nranks, int64_t& lo, int64_t& hi) {
+  VIE_REQUIRE(nranks >= 1 && nranks <= (1 << 20), VIE_EINVAL, "nranks out of range [1, 2^20]");
   int lev = 0;
   while ((1 << lev) < nranks) ++lev;
-  VIE_REQUIRE(nranks >= 1 && (1 << lev) == nranks, VIE_EINVAL, "nranks must be a power of two");
+  VIE_REQUIRE((1 << lev) == nranks, VIE_EINVAL, "nranks must be a power of two");
   VIE_REQUIRE(lev <= h->tree.levels, VIE_EINVAL, "more ranks than leaves of the cluster tree");
   VIE_REQUIRE(rank >= 0 && rank < nranks, VIE_EINVAL, "rank out of range");
   lo = h->tree.bounds[lev][rank];
@@ -70,6 +71,9 @@ extern "C" vie_status vie_shard_range(const vie_op* h, int32_t rank, int32_t nra
   } catch (const Error& e) {
     set_error(e.msg);
     return e.status;
+  } catch (const std::exception& e) {  // no exception leaves the C ABI
+    set_error(e.what());
+    return VIE_EINVAL;
   }
 }
 
