@@ -402,8 +402,9 @@ vie_status vie_server_create(vie_op* const* ops, int32_t nops, int32_t restart, 
                              int64_t mem_budget, void* stream, vie_server** out);
 
 /* Queue a request: V_host is a host c128 N_op x nrhs column-major block (copied
- * now); *id receives the request id.  VIE_ENAN for NaN/Inf input, VIE_ENOMEM
- * when one request alone exceeds the budget. */
+ * now); *id receives the request id.  VIE_EINVAL for nrhs outside [1, 2^20] or
+ * rtol <= 0, VIE_ENAN for NaN/Inf input, VIE_ENOMEM when one request alone
+ * exceeds the budget. */
 vie_status vie_server_submit(vie_server* srv, int32_t op, const void* V_host, int64_t nrhs, double rtol,
                              int64_t* id);
 

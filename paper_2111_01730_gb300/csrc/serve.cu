@@ -598,7 +598,7 @@ vie_status vie_server_create(vie_op* const* ops, int32_t nops, int32_t restart, 
 
 vie_status vie_server_submit(vie_server* sv, int32_t op, const void* V_host, int64_t nrhs, double rtol, int64_t* id) {
   return guarded_s([&] {
-    VIE_REQUIRE(sv && V_host && id && nrhs >= 1 && rtol > 0, VIE_EINVAL, "bad request");
+    VIE_REQUIRE(sv && V_host && id && nrhs >= 1 && nrhs <= (1 << 20) && rtol > 0, VIE_EINVAL, "bad request");
     Server& S = sv->S;
     VIE_REQUIRE(op >= 0 && op < (int)S.ops.size(), VIE_EINVAL, "operator index out of range");
     const int64_t n = S.ops[op]->mesh.nf;
