@@ -141,7 +141,9 @@ typedef struct {
 /* Build Z (and Zinv when cfg->tol_fact > 0) for the voxel body at wavenumber
  * k0 (Sec. III-A construction; Sec. III-B inversion).  Mesh, SWG table and
  * cluster tree are made on the host; entries, IDs and factors on the GPU.
- * Returns VIE_EINVAL for nvox <= 0, h <= 0, leaf < 4, tol_con <= 0. */
+ * Returns VIE_EINVAL for nvox <= 0, h <= 0, leaf < 4, tol_con <= 0, a voxel
+ * index with |i| >= 2^19, a voxel listed twice, or an eps_r that is zero or not
+ * finite. */
 vie_status vie_build(const vie_voxels* body, double k0, const vie_config* cfg,
                      void* stream, vie_op** out);
 

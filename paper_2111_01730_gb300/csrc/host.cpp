@@ -34,6 +34,10 @@ void build_mesh(const vie_voxels& body, Mesh& m) {
   m.eps.assign(body.eps, body.eps + 2 * body.nvox);
   for (int64_t i = 0; i < 3 * body.nvox; ++i)
     VIE_REQUIRE(std::abs(body.ijk[i]) < (1 << 19), VIE_EINVAL, "voxel index out of range (|i| < 2^19)");
+  for (int64_t v = 0; v < body.nvox; ++v)  // kappa = (eps_r - 1) / eps_r needs a finite, nonzero eps_r
+    VIE_REQUIRE(std::isfinite(m.eps[2 * v]) && std::isfinite(m.eps[2 * v + 1]) &&
+                    (m.eps[2 * v] != 0.0 || m.eps[2 * v + 1] != 0.0),
+                VIE_EINVAL, "eps_r must be finite and nonzero");
   m.nt = 6 * m.nvox;
   // vertices: unique lattice points, lexicographic (i, j, k)
   std::vector<uint64_t> keys(4 * m.nt);

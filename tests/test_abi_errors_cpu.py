@@ -127,3 +127,17 @@ def test_load_rejects_a_bad_body_header(lib, tmp_path):
         assert lib.vie_load(os.fsencode(f), None, ctypes.byref(out)) == pkg.VIE_EINVAL
         assert "bad body header" in _msg(lib)
     assert not out.value
+
+
+def test_voxel_body_rejects_zero_or_non_finite_permittivity():
+    """kappa = (eps_r - 1) / eps_r needs a finite, nonzero eps_r (host mesh builder, no GPU)."""
+    import workloads as W
+
+    ijk = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.int32)
+    for bad in (0.0, np.nan, np.inf, complex(1.0, np.nan)):
+        body = W.VoxelBody("bad_eps", 0.1, ijk, np.array([4.0 - 0.5j, bad], dtype=np.complex128))
+        with pytest.raises(pkg.VieError) as e:
+            pkg.mesh_host(body)
+        assert e.value.status == pkg.VIE_EINVAL and "eps_r" in str(e.value)
+    ok = W.VoxelBody("ok", 0.1, ijk, np.array([4.0 - 0.5j, 1.0], dtype=np.complex128))
+    assert len(pkg.mesh_host(ok)["perm"]) > 0
