@@ -174,6 +174,10 @@ extern "C" vie_status vie_load(const char* path, void* stream, vie_op** out) {
     VIE_REQUIRE(std::memcmp(magic, kMagic, sizeof(kMagic)) == 0, VIE_EINVAL, "vie_load: not an operator file");
     h = new vie_op();
     h->cfg = rdv<vie_config>(f);
+    VIE_REQUIRE(h->cfg.leaf >= 4 && h->cfg.tol_con > 0 &&
+                    (h->cfg.factor_dtype == VIE_C64 || h->cfg.factor_dtype == VIE_C128) &&
+                    h->cfg.prec >= VIE_P_AUTO && h->cfg.prec <= VIE_P_TC_TF32,
+                VIE_EINVAL, "vie_load: bad configuration");
     const double k0 = rdv<double>(f), hh = rdv<double>(f);
     const int64_t nvox = rdv<int64_t>(f);
     VIE_REQUIRE((nvox > 0 || nvox == -1) && nvox < (int64_t(1) << 34) && hh > 0 && k0 > 0, VIE_EINVAL,

@@ -127,6 +127,13 @@ def test_load_rejects_a_bad_body_header(lib, tmp_path):
         assert lib.vie_load(os.fsencode(f), None, ctypes.byref(out)) == pkg.VIE_EINVAL
         assert "bad body header" in _msg(lib)
     assert not out.value
+    # a configuration no build accepts (leaf < 4, chi_con <= 0, unknown factor type or precision)
+    for bad in (dict(leaf=2), dict(tol_con=0.0), dict(factor_dtype=7), dict(prec=99)):
+        f = tmp_path / "cfg.vie"
+        f.write_bytes(b"VIEOPv1\0" + bytes(_cfg(**bad)) + np.array([6.28, 0.1]).tobytes()
+                      + np.array([2], dtype=np.int64).tobytes())
+        assert lib.vie_load(os.fsencode(f), None, ctypes.byref(out)) == pkg.VIE_EINVAL
+        assert "bad configuration" in _msg(lib)
 
 
 def test_voxel_body_rejects_zero_or_non_finite_permittivity():
