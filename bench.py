@@ -172,7 +172,8 @@ def oracle_operator():
 
 def oracle_sample_desc(H, n, reps, dt):
     return (f"oracle FP64 HOD-BF apply of a sphere r=0.25 eps_r=4-0.1j pitch 1/16 (N={n}, chi_con=1e-4, "
-            f"{H.entries()} complex128 entries), {reps} applies of {dt * 1e3:.2f} ms")
+            f"{H.entries()} complex128 entries), {reps} applies of {dt * 1e3:.2f} ms; one Python thread "
+            f"driving NumPy, whose BLAS may use up to `cores` threads per block product")
 
 
 def oracle_apply_sample(seconds_budget: float = 15.0):
