@@ -207,3 +207,21 @@ class Brute:
                 one = lambda x: np.ones(x.shape[:-1])
                 z += -1.0 * jump_n * (ws * inner_tri(rs, self.V[self.F[n]], one, k0)).sum()
         return z
+
+
+def _entry_task(args):
+    br, m, n, n_out = args
+    return br.entry(m, n, n_out=n_out)
+
+
+def entries(br: Brute, pairs, n_out=10, procs=None) -> np.ndarray:
+    """br.entry for every (m, n) in pairs, one pair per worker process (started with spawn)."""
+    import multiprocessing as mp
+    import os
+
+    pairs = list(pairs)
+    procs = min(len(pairs), procs or max(1, os.cpu_count() or 1))
+    if procs <= 1:
+        return np.array([br.entry(m, n, n_out=n_out) for m, n in pairs])
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return np.array(pool.map(_entry_task, [(br, m, n, n_out) for m, n in pairs]))

@@ -56,3 +56,29 @@ def z_rows(body, k0, rows, procs: int | None = None, per: int = 4) -> np.ndarray
     with ctx.Pool(min(procs, len(parts))) as pool:
         blocks = pool.map(_some_rows, [(body, k0, r) for r in parts])
     return np.concatenate(blocks, axis=0)
+
+
+def _pair_task(args):
+    from oracle import entries as EN
+    from oracle import quadrature as Q
+    from oracle.entries import Elements, zblock
+
+    mesh, k0, m, n, orders = args
+    near, smooth, far = orders
+    EN.RULES.update({
+        "far_tet": lambda: Q.tet_conical(far), "far_tri": lambda: Q.tri_conical(far),
+        "mid_tet": lambda: Q.tet_conical(far), "mid_tri": lambda: Q.tri_conical(far),
+        "near_tet": lambda: Q.tet_conical(near), "near_tri": lambda: Q.tri_conical(near),
+        "smooth_tet": lambda: Q.tet_conical(smooth), "smooth_tri": lambda: Q.tri_conical(smooth),
+    })
+    return zblock(Elements(mesh, k0), [m], [n])[0, 0]
+
+
+def raised_entries(mesh, k0, pairs, near: int, smooth: int, far: int, procs: int | None = None) -> np.ndarray:
+    """Z(m, n) of the oracle for each pair with every rule raised to conical orders (near, smooth,
+    far), one pair per spawned worker (the rule table is set in the worker, not in the caller)."""
+    pairs = list(pairs)
+    procs = min(len(pairs), procs or max(1, (os.cpu_count() or 2)))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        return np.array(pool.map(_pair_task, [(mesh, k0, m, n, (near, smooth, far)) for m, n in pairs]))

@@ -117,7 +117,7 @@ def probe():
     """Five voxels of different permittivity (charge jumps on every interface, half-SWGs on the
     outside) at near (Chebyshev distance <= 1), mid (2) and far (3) separations; the brute-force
     entries (tests/brute_vie.py) of a selection of face pairs."""
-    from brute_vie import Brute
+    from brute_vie import Brute, entries
 
     ijk = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [3, 0, 0], [0, 0, 3]], dtype=np.int32)
     eps = np.array([4 - 0.5j, 2 - 0.2j, 6 - 1j, 3 - 0.1j, 5 - 0.3j])
@@ -133,8 +133,8 @@ def probe():
             (jump[0], bnd[0]), (bnd[0], inter[0])]
     sep = [(inter[0], far), (bnd[0], mid), (far, jump[0])]
     br = Brute(mesh["verts"], mesh["tets"], mesh["faces"], tp, tm, mesh["eps"], W.K0)
-    zb_near = np.array([br.entry(m, k, n_out=8) for m, k in near])
-    zb_sep = np.array([br.entry(m, k, n_out=5) for m, k in sep])
+    zb_near = entries(br, near, n_out=8)
+    zb_sep = entries(br, sep, n_out=5)
     return E, near, sep, zb_near, zb_sep
 
 
@@ -237,13 +237,14 @@ def test_near_pairs_vs_brute_force_to_1e6(probe):
     observer, smooth remainder): a self pair and a pair across a charge-jump face, the oracle at
     near/smooth orders 30/18 against the brute force at outer order 12 (itself converged to
     1.5e-7 between orders 12 and 14); measured 6.8e-7 and 8.4e-8."""
-    from brute_vie import Brute
+    from brute_vie import Brute, entries
 
     E, near, sep, zb_near, zb_sep = probe
     mesh = E.mesh
     pairs = [near[0], near[3]]  # (interior, interior), (interior, jump)
     br = Brute(mesh["verts"], mesh["tets"], mesh["faces"], mesh["face_tp"], mesh["face_tm"], mesh["eps"], W.K0)
-    zb = np.array([br.entry(m, k, n_out=12) for m, k in pairs])
-    with _raised_rules(near=30, smooth=18, far=8):
-        zo = np.array([zblock(E, [m], [k])[0, 0] for m, k in pairs])
+    zb = entries(br, pairs, n_out=12)
+    from oracle_pool import raised_entries
+
+    zo = raised_entries(mesh, W.K0, pairs, near=30, smooth=18, far=8)
     assert (np.abs(zo - zb) / np.abs(zb)).max() < 1e-6

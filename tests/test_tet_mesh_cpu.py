@@ -40,7 +40,7 @@ def test_general_oracle_reduces_to_the_voxel_path():
 @pytest.fixture(scope="module")
 def jittered():
     """The probe voxels cut into five tets each, every vertex jittered by up to 0.08 h."""
-    from brute_vie import Brute
+    from brute_vie import Brute, entries
 
     tm_ = W.tet_body(_probe_body(), jitter=0.08, seed=3)
     mesh = build_mesh_general(tm_.verts, tm_.tets, tm_.eps)
@@ -56,8 +56,8 @@ def jittered():
             (jump[0], bnd[0]), (bnd[0], inter[0])]
     sep = [(inter[0], far), (bnd[0], mid), (far, jump[0])]
     br = Brute(mesh["verts"], mesh["tets"], mesh["faces"], tp, tm, mesh["eps"], W.K0)
-    zb_near = np.array([br.entry(m, k, n_out=8) for m, k in near])
-    zb_sep = np.array([br.entry(m, k, n_out=5) for m, k in sep])
+    zb_near = entries(br, near, n_out=8)
+    zb_sep = entries(br, sep, n_out=5)
     return E, near, sep, zb_near, zb_sep
 
 
