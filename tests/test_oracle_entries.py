@@ -325,19 +325,27 @@ def test_face_self_term_against_closed_form():
         EN.RULES.update(saved)
 
 
-def test_surface_terms_vs_brute_force_to_1e6():
+@pytest.mark.parametrize("jitter", [0.0, 0.1])
+def test_surface_terms_vs_brute_force_to_1e6(jitter):
     """The scalar-potential terms that half-SWG faces and charge jumps add to an entry, one at a
     time in the near tier: int int g over (tetrahedron, face), (face, tetrahedron) and (face,
     face) pairs where the face is a face of the tetrahedron, touches it at a vertex or an edge,
     or shares an edge with the other face.  The oracle (closed-form potential over the source,
     conical rules over the observer, near/smooth orders 30/18) against the brute force's inner
-    integrals under collapsed Gauss outer rules (converged to 3e-8); measured <= 9.5e-8.  With
+    integrals under collapsed Gauss outer rules (converged to 3e-8); measured <= 1.1e-7.  With
     the face-face self term pinned to its closed form, every term of a boundary entry is pinned
-    to 1e-6; the assembled entries are pinned above at 1e-4."""
+    to 1e-6; the assembled entries are pinned above at 1e-4.  jitter 0: the Kuhn voxel mesh;
+    0.1: the same voxels cut into five tets each with every vertex moved by up to 0.1 h."""
     import brute_vie as BV
+    from oracle.mesh import build_mesh_general
 
     ijk = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=np.int32)
-    mesh = build_mesh(W.VoxelBody("three", 0.1, ijk, np.array([4 - 0.5j, 2 - 0.2j, 6 - 1j])))
+    body = W.VoxelBody("three", 0.1, ijk, np.array([4 - 0.5j, 2 - 0.2j, 6 - 1j]))
+    if jitter:
+        tb = W.tet_body(body, jitter=jitter, seed=11)
+        mesh = build_mesh_general(tb.verts, tb.tets, tb.eps)
+    else:
+        mesh = build_mesh(body)
     E = Elements(mesh, W.K0)
     V, T, F, tp, tm = mesh["verts"], mesh["tets"], mesh["faces"], mesh["face_tp"], mesh["face_tm"]
     f = int(np.nonzero(tm < 0)[0][0])
