@@ -61,3 +61,41 @@ def test_grf_cube_statistics():
         rho = np.mean(a[5:] * a[:-5])
         assert abs(rho - np.exp(-0.5)) < 0.1, (ax, rho)
     assert np.array_equal(W.cube_grf(5.0, 0.1).eps, eps)
+
+
+def test_plane_wave_sets():
+    """Config 3's 8 x 16 (theta, phi) grid with theta-hat and phi-hat polarizations (256 waves)
+    and the serving requests' random waves: unit directions, unit polarizations orthogonal to them."""
+    k, p = W.planewave_grid()
+    assert k.shape == p.shape == (256, 3)
+    assert np.allclose(np.linalg.norm(k, axis=1), 1) and np.allclose(np.linalg.norm(p, axis=1), 1)
+    assert np.allclose((k * p).sum(1), 0, atol=1e-15)
+    assert np.allclose((p[:128] * p[128:]).sum(1), 0, atol=1e-15)  # theta-hat, phi-hat per direction
+    assert np.allclose(np.cross(p[:128], p[128:]), k[:128])       # (theta-hat, phi-hat, khat) right-handed
+    assert len(np.unique(np.round(k[:128], 12), axis=0)) == 128
+    th = np.arccos(np.clip(k[:128, 2], -1, 1))
+    assert np.allclose(np.unique(np.round(th, 12)), (np.arange(8) + 0.5) * np.pi / 8)
+    k, p = W.planewave_random(2000, seed=3)
+    assert np.allclose(np.linalg.norm(k, axis=1), 1) and np.allclose(np.linalg.norm(p, axis=1), 1)
+    assert np.abs((k * p).sum(1)).max() < 1e-14
+    assert np.abs(k.mean(0)).max() < 0.06  # uniform on the sphere: mean direction ~ 0 (3 sigma ~ 0.04)
+    k2, p2 = W.planewave_random(2000, seed=3)
+    assert np.array_equal(k, k2) and np.array_equal(p, p2)
+
+
+def test_layered_bodies_and_equal_volume_radii():
+    """Layered spheres assign each voxel the permittivity of the layer holding its centre; the
+    equal-volume radius of a staircase layer holds exactly the volume of its voxels."""
+    body = W.five_layer_sphere()
+    c = (body.ijk.astype(np.float64) + 0.5) * body.h
+    r = np.linalg.norm(c, axis=1)
+    radii, values = [0.5, 0.4, 0.3, 0.2, 0.1], [2.0, 3.0, 4.0, 5.0, 6.0]
+    for i, e in enumerate(values):
+        lo = radii[i + 1] if i + 1 < len(radii) else 0.0
+        sel = (r < radii[i]) & (r >= lo)
+        assert sel.any() and np.all(body.eps[sel] == e)
+    h = 1.0 / 20
+    for R, Req in zip(radii, W.equal_volume_layers(h, radii)):
+        cnt = np.count_nonzero(r < R)
+        assert abs(4.0 / 3.0 * np.pi * Req ** 3 - cnt * h ** 3) < 1e-12
+        assert abs(Req - R) < h
